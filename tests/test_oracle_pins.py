@@ -1,0 +1,324 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these re-type the oracle's own formula: each compares it with a hand
+derivation, a closed form reached another way, a library routine, an
+invariant, a special case, or brute force on tiny inputs.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.stats
+
+from oracle import tsk_oracle as o
+from paper_2311_03393_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_cases(name):
+    cases, cur = {}, None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            if key == "case":
+                cur = cases.setdefault(vals[0], {})
+            else:
+                cur.setdefault(key, []).append([float(v) for v in vals])
+    return cases
+
+
+# --- Def. 3/6: hand-derived profiles ----------------------------------------
+
+@pytest.mark.parametrize("name", ["alternating", "alternating_wide", "spikes_const", "spikes"])
+def test_golden_tiny_profiles(name):
+    c = _read_cases("tiny_mp.txt")[name]
+    x = np.array(c["x"][0])
+    m, excl = int(c["m"][0][0]), int(c["excl"][0][0])
+    P, I = o.mp_selfjoin(x, m, excl)
+    np.testing.assert_allclose(P, np.array(c["P"][0]), rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(I, np.array(c["I"][0], dtype=np.int64))
+
+
+def test_closed_form_matches_direct_distance():
+    """dist^2 = 2 m (1 - rho) with rho from numpy's Pearson correlation (library routine)."""
+    rng = np.random.default_rng(1)
+    for m in (4, 17, 100):
+        for _ in range(50):
+            a = np.cumsum(rng.normal(size=m)) * rng.uniform(0.1, 10) + rng.normal() * 100
+            b = rng.normal(size=m) + 0.5 * a
+            rho = np.corrcoef(a, b)[0, 1]
+            assert o.zdist(a, b) == pytest.approx(math.sqrt(max(0.0, 2 * m * (1 - rho))), rel=1e-10, abs=1e-10)
+
+
+def test_window_stats_match_library():
+    rng = np.random.default_rng(2)
+    x = np.cumsum(rng.normal(size=500))
+    m = 37
+    Z, mu, sd, const = o.znorm_windows(x, m)
+    for i in (0, 1, 100, 463):
+        w = x[i:i + m]
+        assert mu[i] == pytest.approx(np.mean(w), rel=1e-13)
+        assert sd[i] == pytest.approx(np.std(w), rel=1e-12)
+        np.testing.assert_allclose(Z[i], scipy.stats.zscore(w), rtol=1e-10, atol=1e-12)
+    assert not const.any()
+
+
+def test_brute_force_tiny_against_itertools():
+    """Profile vs an explicit enumeration of all admissible pairs with library z-scores."""
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=23)
+    m, excl = 5, 2
+    l = len(x) - m + 1
+    zs = [scipy.stats.zscore(x[i:i + m]) for i in range(l)]
+    P, I = o.mp_selfjoin(x, m, excl)
+    for i in range(l):
+        best, arg = math.inf, -1
+        for j in range(l):
+            if abs(i - j) >= excl:
+                dd = float(np.linalg.norm(zs[i] - zs[j]))
+                if dd < best:
+                    best, arg = dd, j
+        assert P[i] == pytest.approx(best, rel=1e-12)
+        assert I[i] == arg
+
+
+def test_periodic_signal_has_zero_profile():
+    """An exactly periodic stream (period p > excl) has an exact repeat for every window."""
+    p, m = 25, 40
+    t = np.arange(m + 3 * p)
+    x = np.sin(2 * np.pi * t / p) + 0.3 * np.cos(4 * np.pi * t / p)
+    P, I = o.mp_selfjoin(x, m, o_excl := math.ceil(m / 4))
+    assert o_excl < p
+    assert np.all(P < 1e-6)
+    assert np.all(np.abs(np.abs(I - np.arange(len(I))) % p) == 0)
+
+
+def test_white_noise_profile_scale():
+    """For i.i.d. noise the pairwise correlations concentrate at 0, distances at sqrt(2m)."""
+    rng = np.random.default_rng(4)
+    m = 64
+    x = rng.normal(size=3000)
+    W = np.lib.stride_tricks.sliding_window_view(x, m)[::97]
+    Z = scipy.stats.zscore(W, axis=1)
+    d = [np.linalg.norm(Z[a] - Z[b]) for a in range(len(Z)) for b in range(a + 1, len(Z))]
+    assert np.median(d) == pytest.approx(math.sqrt(2 * m), rel=0.05)
+    P, _ = o.mp_rows(x, m, 16, [10, 1500, 2900])
+    assert np.all(P < math.sqrt(2 * m)) and np.all(P > 0.5 * math.sqrt(2 * m))
+
+
+def test_profile_invariant_to_scale_sign_shift():
+    rng = np.random.default_rng(5)
+    x = np.cumsum(rng.normal(size=300))
+    m, excl = 20, 5
+    P0, I0 = o.mp_selfjoin(x, m, excl)
+    for c, b in ((3.5, -7.0), (-0.01, 1e3), (-1.0, 0.0)):
+        P1, I1 = o.mp_selfjoin(c * x + b, m, excl)
+        np.testing.assert_allclose(P1, P0, rtol=1e-7, atol=1e-7)
+        np.testing.assert_array_equal(I1, I0)
+
+
+def test_constant_window_rules_against_hand_values():
+    x = np.concatenate([np.full(10, 3.0), np.arange(10.0), np.full(10, 3.0)])
+    m, excl = 5, 2
+    P, I = o.mp_selfjoin(x, m, excl)
+    l = len(x) - m + 1
+    const = [np.ptp(x[i:i + m]) == 0 for i in range(l)]
+    for i in range(l):
+        if const[i]:
+            assert P[i] == 0.0 and const[I[i]]
+        else:
+            assert P[i] <= math.sqrt(m) + 1e-12
+
+
+# --- Sec. III-A: z-normalisation and sketch ----------------------------------
+
+def test_global_znorm_matches_scipy_zscore():
+    T, _ = synth.random_walks(6, 700, 50, 1, seed=6, dtype=np.float64)
+    Tbar, mu, sigma = o.global_znorm(T)
+    np.testing.assert_allclose(Tbar, scipy.stats.zscore(T, axis=1, ddof=0), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(sigma, np.std(T, axis=1), rtol=1e-12)
+
+
+def test_fig1_sum_of_streams_is_the_k1_sketch_and_keeps_the_discord():
+    """Fig. 1: the MP of the sum of z-normalised streams still shows a discord of one stream."""
+    n, m = 1200, 60
+    rng = np.random.default_rng(7)
+    t = np.arange(n)
+    T = np.stack([np.sin(2 * np.pi * t / 50 + ph) + 0.05 * rng.normal(size=n)
+                  for ph in rng.uniform(0, 6.28, size=5)])
+    p = 600
+    T[0, p:p + m] = rng.normal(size=m) * 0.5
+    R = np.ones((5, 1))
+    Tbar, _, _ = o.global_znorm(T)
+    S = o.sketch(Tbar, R)
+    np.testing.assert_allclose(S[0], np.sum(scipy.stats.zscore(T, axis=1), axis=0), rtol=1e-10, atol=1e-10)
+    res = o.discord_topk(*o.profile_streams(S, m, m // 4), K=1, topk_excl=m)
+    assert abs(res[0][0] - p) <= m
+
+
+def test_count_sketch_permutation_gives_the_exact_profiles():
+    """k = d with h a permutation: every sketch stream is +-T_bar_j, so its MP is T_j's MP."""
+    d, n, m = 5, 400, 24
+    T, _ = synth.random_walks(d, n, m, 1, seed=8, dtype=np.float64)
+    h = np.array([2, 4, 1, 0, 3])          # not an involution: catches a transposed R
+    s = np.array([1, -1, -1, 1, -1])
+    R = np.zeros((d, d))
+    R[np.arange(d), h] = s
+    Tbar, _, _ = o.global_znorm(T)
+    S = o.sketch(Tbar, R)
+    np.testing.assert_allclose(S, o.sketch_alg1(Tbar, h, s, d), rtol=0, atol=1e-13)
+    for j in range(d):
+        Pe, Ie = o.mp_selfjoin(T[j], m, 6)
+        Ps, Is = o.mp_selfjoin(S[h[j]], m, 6)
+        np.testing.assert_allclose(Ps, Pe, rtol=1e-7, atol=1e-7)
+
+
+def test_dimension_delete_then_add_equals_rebuild():
+    """Sec. III-C linearity: removing then re-adding a dimension restores the sketch."""
+    d, n, k = 7, 500, 3
+    T, _ = synth.random_walks(d, n, 20, 0, seed=9, dtype=np.float64)
+    R = synth.gaussian_R(d, k, 10).astype(np.float64)
+    for bf16 in (False, True):
+        S = o.sketch(o.global_znorm(T)[0], R, bf16=bf16)
+        S_minus = o.update_dims(S, T[[2, 5]], R[[2, 5]], [-1, -1], bf16=bf16)
+        keep = [0, 1, 3, 4, 6]
+        np.testing.assert_allclose(S_minus, o.sketch(o.global_znorm(T[keep])[0], R[keep], bf16=bf16),
+                                   rtol=0, atol=1e-12)
+        S_back = o.update_dims(S_minus, T[[2, 5]], R[[2, 5]], [1, 1], bf16=bf16)
+        np.testing.assert_allclose(S_back, S, rtol=0, atol=1e-12)
+
+
+def test_lemma1_count_sketch_unbiased_with_stated_variance():
+    """Lemma 1: E[s(j) S^(h(j))_i] = T_bar^(j)_i, Var = (1/k) sum_{j' != j} (T_bar^(j')_i)^2."""
+    d, k, n = 12, 4, 6
+    rng = np.random.default_rng(11)
+    Tbar = rng.normal(size=(d, n))
+    draws = 6000
+    est = np.empty((draws, d, n))
+    for r in range(draws):
+        h, s = synth.count_sketch_hashes(d, k, seed=1000 + r)
+        S = o.sketch_alg1(Tbar, h, s, k)
+        est[r] = s[:, None] * S[h]
+    mean = est.mean(axis=0)
+    var = est.var(axis=0)
+    want_var = (np.sum(Tbar ** 2, axis=0)[None, :] - Tbar ** 2) / k
+    se = np.sqrt(want_var / draws)
+    assert np.all(np.abs(mean - Tbar) < 5 * se + 1e-12)
+    np.testing.assert_allclose(var, want_var, rtol=0.12)
+
+
+# --- Def. 5 / Alg. 2 ---------------------------------------------------------
+
+def test_aggregate_and_topk_tie_rules():
+    rows = {}
+    with open(os.path.join(GOLDEN, "topk_ties.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                key, *vals = line.split()
+                rows.setdefault(key, []).append([float(v) for v in vals])
+    P = np.array(rows["P"])
+    I = np.array(rows["I"], dtype=np.int64)
+    K, te = int(rows["K"][0][0]), int(rows["topk_excl"][0][0])
+    res = o.discord_topk(P, I, K, te)
+    want = [(int(r[0]), int(r[1]), r[2], int(r[3])) for r in rows["R"]]
+    assert res == want
+
+
+def test_all_zero_scores_return_group_zero():
+    """Alg. 2 starts from a best-so-far of 0 with a strict '>': all-zero scores give g = 0."""
+    P = np.zeros((3, 5))
+    I = np.zeros((3, 5), dtype=np.int64)
+    res = o.discord_topk(P, I, 1, 2)
+    assert res[0][:3] == (0, 0, 0.0)
+
+
+def test_planted_discord_is_the_discord_of_its_stream():
+    """Sanity on the small random-walk workload: the planted stream's own discord is the planted window.
+
+    (Random walks carry natural discords of similar size, so the planted one
+    need not be the top across all streams; the paper notes this difficulty.)
+    """
+    wl = synth.workload(1)
+    T = wl.series[0]
+    (_, j, p), = wl.planted
+    excl = synth.default_excl(wl.m)
+    P, I = o.mp_selfjoin(T[j], wl.m, excl)
+    assert abs(int(np.argmax(P)) - p) <= wl.m
+
+
+# --- adjoint -----------------------------------------------------------------
+
+def test_adjoint_matches_central_differences_of_full_forward():
+    d, n, m, k, K = 5, 260, 16, 3, 2
+    T, _ = synth.random_walks(d, n, m, 2, seed=12, dtype=np.float64)
+    R = synth.gaussian_R(d, k, 13).astype(np.float64)
+    excl = synth.default_excl(m)
+    res, S, P, I = o.sketched_discords(T, R, m, excl, K, m)
+    sel = [(i, g, nn) for (i, g, _, nn) in res]
+    dT, dR = o.grad_selected(T, R, sel, m)
+    rng = np.random.default_rng(14)
+    support = [(j, t) for (i, g, nn) in sel for j in range(d) for t in list(range(i, i + m)) + list(range(nn, nn + m))]
+    cT = [support[q] for q in rng.choice(len(support), 20, replace=False)] + \
+         [tuple(v) for v in zip(rng.integers(0, d, 10), rng.integers(0, n, 10))]
+    fdT = o.central_difference(lambda X: o.topk_loss(X, R, m, excl, K, m), T, cT, 1e-5)
+    got = np.array([dT[c] for c in cT])
+    np.testing.assert_allclose(got, fdT, rtol=1e-5, atol=1e-7)
+    cR = [(j, g) for j in range(d) for g in range(k)]
+    fdR = o.central_difference(lambda X: o.topk_loss(T, X, m, excl, K, m), R, cR, 1e-5)
+    np.testing.assert_allclose([dR[c] for c in cR], fdR, rtol=1e-5, atol=1e-7)
+
+
+def test_fixed_selection_loss_equals_topk_loss():
+    d, n, m, k, K = 4, 220, 12, 2, 2
+    T, _ = synth.random_walks(d, n, m, 1, seed=15, dtype=np.float64)
+    R = synth.gaussian_R(d, k, 16).astype(np.float64)
+    excl = synth.default_excl(m)
+    res, _, _, _ = o.sketched_discords(T, R, m, excl, K, m)
+    sel = [(i, g, nn) for (i, g, _, nn) in res]
+    assert o.selected_loss(T, R, sel, m) == pytest.approx(o.topk_loss(T, R, m, excl, K, m), rel=1e-12)
+
+
+# --- number format and counting ---------------------------------------------
+
+def test_bf16_round_matches_torch_for_float32_inputs():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(17)
+    x = np.concatenate([
+        rng.normal(size=20000).astype(np.float32),
+        (rng.normal(size=2000) * 1e-30).astype(np.float32),
+        (rng.normal(size=2000) * 1e30).astype(np.float32),
+        np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8), 2 ** -130, 0.0, -0.0], dtype=np.float32),
+    ])
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(o.bf16_round(x.astype(np.float64)), want)
+
+
+def test_bf16_round_float64_ties_to_even_exactly():
+    """Rounding from float64 (not via float32) checked with exact rationals."""
+    rng = np.random.default_rng(18)
+    vals = list(rng.normal(size=300) * 10.0 ** rng.integers(-5, 5, size=300))
+    vals += [1 + 2 ** -8, 1 + 2 ** -8 + 2 ** -40, 1 + 3 * 2 ** -8, 1 + 2 ** -8 - 2 ** -45]
+    for v in vals:
+        v = float(v)
+        e = math.frexp(abs(v))[1]
+        ulp = Fraction(2) ** (e - 8)
+        q = Fraction(abs(v)) / ulp
+        lo = math.floor(q)
+        rem = q - lo
+        r = lo + (1 if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and lo % 2 == 1) else 0)
+        want = math.copysign(float(r * ulp), v)
+        assert o.bf16_round(np.array([v]))[0] == want, v
+
+
+def test_cell_count_by_enumeration():
+    for n, m, excl in ((50, 7, 2), (31, 5, 10), (12, 12, 1), (40, 10, 3)):
+        l = n - m + 1
+        brute = sum(1 for i in range(l) for j in range(i + 1, l) if j - i >= excl)
+        assert o.cells(n, m, excl) == brute
