@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the sketched discord-mining path on GB300.
+
+One step is one pass of the whole path over one batch of synthetic input:
+  sketch build (global z-normalisation + S = R^T T_bar, bfloat16 tensor cores)
+  -> matrix profile of the k sketch streams -> aggregation + top-K discords
+  -> adjoint of the discord scores
+  -> delete one dimension (rank-one update) -> re-profile the changed sketch
+     streams -> top-K
+  -> exact d-dimensional matrix profile of the raw streams -> top-K.
+The metric is matrix-profile cell-updates per second over the step (a cell is
+one unordered window pair (i, j), j - i >= excl); the step's parts are timed
+too, giving the sketched vs exact discord-mining times.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload water]
+  python bench.py --impl reference ...     (the FP64 CPU oracle on host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MP cell-updates/s and discord-mining time: sketched vs exact d-dim MP, 1 GB300"
+UNIT = "cell-updates/s"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20
+# Per-cell DRAM traffic of k_mp_diag from an ncu capture (None until taken for
+# the current kernel); see profiles/mp_diag_ncu.md.
+MP_DIAG_DRAM_BYTES_PER_CELL = None
+
+WORKLOADS = {
+    # name: (synth workload index, top-K, description)
+    "water": (2, 5, "water-plant-like sensors d=51 n=50000 m=100 k=8 (5 planted discords)"),
+    "traffic": (3, 10, "traffic-like sensors d=1024 n=100000 m=144 k=16 (10 planted discords)"),
+    "grad": (5, 3, "random walks d=64 n=20000 m=100 k=8 (3 planted discords)"),
+    "rw_small": (1, 3, "random walks d=8 n=2000 m=100 k=4 (1 planted discord)"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--workload", default="water", choices=list(WORKLOADS))
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the timed oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in self.rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+
+def cells_per_stream(n: int, m: int, excl: int) -> int:
+    l = n - m + 1
+    e = l - excl
+    return max(0, e) * max(0, e + 1) // 2
+
+
+def build_workload(name: str, rank: int):
+    from paper_2311_03393_gb300 import dist, synth
+    idx, K, desc = WORKLOADS[name]
+    wl = synth.workload(idx, seed=dist.replica_seed(synth.SEED_BASE + idx, rank))
+    return wl, K, desc
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, seconds: float, rng_seed: int = 0):
+    """Time the oracle's profile rows of the sketched streams until `seconds` pass.
+
+    Returns (cells, elapsed, rows, description).  Cells count unordered pairs:
+    one oracle row evaluates every admissible j, i.e. two half-pairs per cell.
+    """
+    from oracle import tsk_oracle as o
+    T = wl.series[0]
+    m = wl.m
+    excl = int(math.ceil(m / 4))
+    t0 = time.perf_counter()
+    Tbar, _, _ = o.global_znorm(T)
+    S = o.sketch(Tbar, wl.R, bf16=True)
+    n = T.shape[1]
+    l = n - m + 1
+    rng = np.random.default_rng(rng_seed)
+    half_pairs = 0
+    rows = 0
+    while time.perf_counter() - t0 < seconds:
+        g = int(rng.integers(0, S.shape[0]))
+        i = int(rng.integers(0, l))
+        o.mp_rows(S[g], m, excl, [i])
+        lo, hi = max(0, i - excl + 1), min(l, i + excl)
+        half_pairs += l - (hi - lo)
+        rows += 1
+    el = time.perf_counter() - t0
+    desc = (f"oracle (numpy float64) sketch of the whole series + {rows} random matrix-profile rows of the "
+            f"{S.shape[0]} sketch streams (n={n}, m={m}), {el:.1f} s")
+    return half_pairs / 2.0, el, rows, desc
+
+
+def run_reference(args):
+    from paper_2311_03393_gb300 import dist
+    rank, _, ws = dist.world()
+    if rank != 0:
+        return 0
+    wl, K, desc = build_workload(args.workload, 0)
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(wl, per_step / 4)
+    cells = el = 0.0
+    descs = []
+    for s in range(args.steps):
+        c, e, _, d = oracle_sample(wl, per_step, rng_seed=s + 1)
+        cells += c
+        el += e
+        descs.append(d)
+    value = cells / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "sample": "random profile rows per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": descs[0]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_2311_03393_gb300 import build, dist
+    rank, local_rank, ws = dist.world()
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    import paper_2311_03393_gb300 as tsk
+
+    wl, K, desc = build_workload(args.workload, rank)
+    T_np = wl.series[0]
+    d, n = T_np.shape
+    m, k = wl.m, wl.k
+    excl = int(math.ceil(m / 4))
+    lens = [n]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T_host = torch.from_numpy(np.ascontiguousarray(T_np.astype(np.float32).ravel())).pin_memory()
+    T = T_host.to(dev)
+    R = torch.from_numpy(wl.R).to(dev)
+    del_dim = d // 2
+    R_del = wl.R[del_dim:del_dim + 1]
+    slen_k = [n] * k
+    slen_d = [n] * d
+    S = torch.empty(k * n, dtype=torch.float32, device=dev)
+    stats = torch.empty((1, d, 2), dtype=torch.float64, device=dev)
+    bufs = {name: (torch.empty(cnt * n, dtype=torch.float32, device=dev),
+                   torch.empty(cnt * n, dtype=torch.int32, device=dev))
+            for name, cnt in (("s", k), ("u", k), ("e", d))}
+    dscore = torch.ones((1, K), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(Tin, ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        tsk.ts_sketch_build(Tin, R, lens, d, precision="bf16", out=S, stats=stats)
+        Ps, Is = tsk.mp_selfjoin(S, slen_k, m, excl, P=bufs["s"][0], I=bufs["s"][1])
+        top_s = tsk.discord_topk(Ps, Is, lens, k, m, K)
+        mark(1)
+        idx, grp, score, nn = top_s
+        tsk.mp_backward(dscore, idx, grp, nn, Tin, stats, R, S, lens, d, m)
+        mark(2)
+        dirty, _ = tsk.ts_sketch_update_dims(S, Tin[del_dim * n:(del_dim + 1) * n], lens, R_del, [-1])
+        Pu, Iu = tsk.mp_selfjoin(S, slen_k, m, excl, mask=dirty, P=bufs["u"][0], I=bufs["u"][1])
+        top_u = tsk.discord_topk(Pu, Iu, lens, k, m, K)
+        mark(3)
+        Pe, Ie = tsk.mp_selfjoin(Tin, slen_d, m, excl, P=bufs["e"][0], I=bufs["e"][1])
+        top_e = tsk.discord_topk(Pe, Ie, lens, d, m, K)
+        mark(4)
+        return top_s, top_u, top_e, dirty
+
+    cps = cells_per_stream(n, m, excl)
+    for _ in range(args.warmup):
+        _, _, _, dirty = step(T)
+    torch.cuda.synchronize()
+    n_dirty = int(np.sum(dirty))
+    cells_step = cps * (k + n_dirty + d)
+    cells_sketched = cps * k
+
+    # --- device-timed steps (inputs resident in HBM, L2 flushed before each step)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    tsk.profile_enable(True)
+    tsk.profile_read("mp_diag")
+    tsk.profile_read("sketch")
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = tsk.launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            step(T, ev[s])
+        torch.cuda.synchronize()
+    launches = tsk.launch_count() - launches0
+    tsk.profile_enable(False)
+    mp_ms, mp_launches = tsk.profile_read("mp_diag")
+    sk_ms, sk_launches = tsk.profile_read("sketch")
+    part = np.array([[ev[s][i].elapsed_time(ev[s][i + 1]) for i in range(4)] for s in range(args.steps)])
+    step_ms = part.sum(axis=1)
+    t_max, cells_sum = dist.reduce_max_sum(float(step_ms.sum()), float(cells_step * args.steps))
+    value = cells_sum / (t_max / 1000.0)
+    ms_per_step = t_max / args.steps
+
+    # --- end to end through the public API: pinned host T in, discords out
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty(3 * 4 * K, dtype=torch.float32).pin_memory()
+        h2d = T_host.numel() * 4
+        d2h = out_host.numel() * 4
+        Tdev = torch.empty_like(T)
+        for _ in range(2):
+            Tdev.copy_(T_host, non_blocking=True)
+            step(Tdev)
+        torch.cuda.synchronize()
+        e_ms = []
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Tdev.copy_(T_host, non_blocking=True)
+            top_s, top_u, top_e, _ = step(Tdev)
+            res = torch.cat([torch.stack([t[1].float().ravel(), t[0].float().ravel(), t[2].float().ravel(),
+                                          t[3].float().ravel()]).ravel() for t in (top_s, top_u, top_e)])
+            out_host.copy_(res, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        te_max, _ = dist.reduce_max_sum(float(np.sum(e_ms)), 0.0)
+        e2e = {"value": cells_sum / (te_max / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    peaks, peak_kind = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sm_count * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12  # T FMA-pipe lane-ops/s
+    cells_in_mp = cps * (k + n_dirty + d) * args.steps
+    achieved = 4.0 * cells_in_mp / (mp_ms / 1000.0) / 1e12 if mp_ms > 0 else None
+    traffic = None
+    if MP_DIAG_DRAM_BYTES_PER_CELL is not None and mp_launches:
+        traffic = MP_DIAG_DRAM_BYTES_PER_CELL * cells_in_mp / mp_launches
+    clocks = clk.summary()
+    sketch_bytes = (2 * 4 * d * n + 4 * k * n)  # stats pass + sketch pass over T, write S
+    sketch_flops = 2.0 * d * k * n
+    sketch_info = None
+    if sk_ms > 0:
+        per = sk_ms / sk_launches / 1000.0
+        sketch_info = {"kernel": "k_sketch_bf16", "ms_per_launch": per * 1000.0,
+                       "hbm_gbs": (4 * d * n + 4 * k * n) / per / 1e9,
+                       "hbm_frac": (4 * d * n + 4 * k * n) / per / 1e9 / peaks["hbm_gbs"],
+                       "bf16_tflops": sketch_flops / per / 1e12,
+                       "bf16_frac": sketch_flops / per / 1e12 / peaks["bf16_tflops"]}
+    parts = part.mean(axis=0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "parallelism": f"replicas{ws}", "sketch": "bf16 tensor cores, f32 accumulate",
+                   "mp": "f32 diagonal recurrence, f64 anchors and refinement", "l2": "flushed before each step",
+                   "cells_per_step": cells_step, "top_k": K},
+        "parts_ms": {"sketched_mining": parts[0], "adjoint": parts[1], "dim_update_and_reprofile": parts[2],
+                     "exact_mining": parts[3]},
+        "speedup_exact_over_sketched": parts[3] / parts[0] if parts[0] > 0 else None,
+        "sketched_mining_cells_per_s": cells_sketched / (parts[0] / 1000.0),
+        "roofline": {"bound": "alu", "kernel": "k_mp_diag", "achieved": achieved, "peak": alu_peak,
+                     "unit": "Tops/s", "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
+                     "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {clock_mhz:.0f} MHz "
+                                   f"({peak_kind} max clock); 4 FMA-pipe ops per cell",
+                     "ms_per_launch": mp_ms / mp_launches if mp_launches else None},
+        "sketch_kernel": sketch_info,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": e2e,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        c, el, rows, sdesc = oracle_sample(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": c / el, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

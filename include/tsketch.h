@@ -1,0 +1,223 @@
+/*
+ * tsketch.h - C ABI of the GB300 sketched discord miner.
+ *
+ * Implements, on one GPU, the data-parallel path of Yeh et al., "Sketching
+ * Multidimensional Time Series for Fast Discord Mining" (arXiv 2311.03393):
+ * the random-projection sketch S = R^T T_bar of d z-normalised streams into k
+ * sketch streams (Sec. III-A, Alg. 1), the self-join matrix profile of every
+ * stream (Def. 6), aggregation over streams (Def. 5), the ranked discords
+ * (Alg. 2), dimension addition/deletion by linearity (Sec. III-C) and the
+ * adjoint of the discord scores.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All array arguments are DEVICE pointers owned by the caller unless the
+ *    parameter name ends in _host.  The library never frees caller memory.
+ *  - Every call is asynchronous on the context's CUDA stream and returns a
+ *    tsk_status; nothing throws across the ABI.  On failure the reason is in
+ *    tsk_last_error(ctx).  Argument errors are detected on the host before
+ *    any launch and leave the outputs untouched.
+ *  - Batch layout: a batch holds n_series independent multivariate series.
+ *    Series s has d streams of series_len_host[s] samples each, stored
+ *    stream-major and packed back to back: element (s, j, t) of T lives at
+ *        T[d * cum[s] + j * len[s] + t],  cum[s] = sum_{s' < s} len[s'].
+ *    A sketch uses the same packing with k streams in place of d.
+ *    All streams of one series have the same length (Sec. III-C advises that
+ *    only streams starting at the same time be combined).
+ *  - Stream layout (matrix profile calls): n_streams streams of
+ *    stream_len_host[q] samples packed back to back, X[cum[q] + t].  Per
+ *    stream the profile has l = len - m + 1 entries; P and I use the same
+ *    packing as X (entry i of stream q at cum[q] + i) and the entries
+ *    i >= l of each stream are set to NaN / -1.
+ *  - Workspace: the context owns a grow-only device workspace.  A call that
+ *    needs more than it holds allocates (cudaMalloc) first; call
+ *    tsk_reserve() beforehand when the calls will be captured in a CUDA graph
+ *    (growing during capture fails with TSK_ERR_OOM).
+ *  - Device-side problems (non-finite input) set an error word that
+ *    tsk_sync() reports as TSK_ERR_NONFINITE.  No kernel traps or spins.
+ */
+#ifndef TSKETCH_H
+#define TSKETCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSK_API __attribute__((visibility("default")))
+
+typedef int32_t tsk_status;
+enum {
+  TSK_OK = 0,
+  TSK_ERR_INVALID_ARG = 1,  /* bad shape, size, pointer or enum; nothing launched      */
+  TSK_ERR_CUDA = 2,         /* a CUDA runtime call failed (message has the CUDA error) */
+  TSK_ERR_OOM = 3,          /* workspace could not grow                                */
+  TSK_ERR_UNSUPPORTED = 4,  /* valid request outside what this build implements        */
+  TSK_ERR_TIMEOUT = 5,      /* tsk_sync deadline passed before the stream drained      */
+  TSK_ERR_NONFINITE = 6     /* a kernel met NaN/Inf in its input                        */
+};
+
+/* element types of input series */
+enum { TSK_F32 = 0, TSK_F64 = 1 };
+
+/* arithmetic of the sketch S = R^T T_bar */
+enum {
+  TSK_SKETCH_BF16 = 0, /* T_bar and R rounded to bfloat16 (nearest even, from the
+                          float64 value), products summed in float32 on tensor cores;
+                          S is float32                                             */
+  TSK_SKETCH_FP32 = 1, /* float32 products and sums; S is float32                   */
+  TSK_SKETCH_FP64 = 2  /* float64 throughout; S is float64                          */
+};
+
+/* arithmetic of the matrix profile */
+enum {
+  TSK_MP_FP32 = 0, /* float32 diagonal recurrence with float64 anchors and a float64
+                      re-evaluation of every row's chosen neighbour; P is float32  */
+  TSK_MP_FP64 = 1  /* float64 throughout; P is float64                            */
+};
+
+typedef struct tsk_ctx tsk_ctx;
+
+/* Create a context on `device`, issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  *ctx receives the handle. */
+TSK_API tsk_status tsk_create(tsk_ctx** ctx, int32_t device, void* cuda_stream);
+/* Switch the stream later calls are issued on. */
+TSK_API tsk_status tsk_set_stream(tsk_ctx* ctx, void* cuda_stream);
+/* Free the context and its workspace (waits for the stream first). */
+TSK_API void tsk_destroy(tsk_ctx* ctx);
+/* Text of the last error on this context ("" if none).  Valid until the next call. */
+TSK_API const char* tsk_last_error(const tsk_ctx* ctx);
+/* Grow the workspace to at least `bytes` now (use before graph capture). */
+TSK_API tsk_status tsk_reserve(tsk_ctx* ctx, size_t bytes);
+/* Bytes of workspace mp_selfjoin needs for this stream layout. */
+TSK_API tsk_status tsk_mp_workspace_bytes(tsk_ctx* ctx, int32_t n_streams, const int32_t* stream_len_host,
+                                          int32_t m, size_t* bytes_out);
+/* Wait until the stream drains, at most timeout_s seconds (<= 0: no limit),
+ * then read and clear the device error word.  TSK_ERR_TIMEOUT if the deadline
+ * passed (the work keeps running; call again). */
+TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s);
+/* Rows per matrix-profile work unit (a band of diagonals x `rows` rows);
+ * a multiple of 8 in [8, 1 << 20].  Smaller units balance short streams,
+ * larger ones amortise the float64 anchors.  Default 2048. */
+TSK_API tsk_status tsk_set_tile_rows(tsk_ctx* ctx, int32_t rows);
+/* Number of kernels this context has launched since creation. */
+TSK_API int64_t tsk_launch_count(const tsk_ctx* ctx);
+
+/* Kernel timing: when enabled, CUDA events are recorded on the context
+ * stream around every launch of the named kernels (not during graph capture).
+ * tsk_profile_read waits for them, returns the summed device time and the
+ * launch count since the last read, and clears them. */
+enum { TSK_PROF_MP_DIAG = 0, TSK_PROF_SKETCH = 1, TSK_PROF_COUNT = 2 };
+TSK_API tsk_status tsk_profile_enable(tsk_ctx* ctx, int32_t enable);
+TSK_API tsk_status tsk_profile_read(tsk_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches);
+
+/*
+ * ts_sketch_build - global z-normalisation and the sketch (Sec. III-A, Alg. 1).
+ *
+ *   mu[s][j], sigma[s][j] = mean and population std of stream j of series s
+ *   T_bar[s][j][t]        = (T[s][j][t] - mu) / sigma   (0 for a constant stream)
+ *   S[s][g][t]            = sum_j R[j][g] * T_bar[s][j][t]
+ *
+ * Alg. 1 is the special case of a count-sketch R (one +-1 per row, at column
+ * h(j)); any dense R (e.g. Gaussian) is accepted.
+ *   T      : input series, batch layout with d streams, element type t_dtype.
+ *   R      : float32, d x k row-major, shared by all series.
+ *   S      : output sketch, batch layout with k streams; float32, or float64
+ *            when precision == TSK_SKETCH_FP64.
+ *   stats  : output float64 [n_series][d][2] = {mu, sigma}; may be NULL.
+ * Requires n_series >= 1, d >= 1, 1 <= k <= 64, every len >= 1.
+ */
+TSK_API tsk_status ts_sketch_build(tsk_ctx* ctx, const void* T, int32_t t_dtype, int32_t n_series,
+                                   const int32_t* series_len_host, int32_t d, const float* R, int32_t k,
+                                   int32_t precision, void* S, double* stats);
+
+/*
+ * ts_sketch_update_dims - add or delete dimensions by linearity (Sec. III-C).
+ *
+ * For each listed dimension q (raw streams T_dims, batch layout with nd
+ * streams per series): z-normalise it over its whole length and apply
+ *   S[s][g][t] += op[q] * R_rows[q][g] * T_bar_dims[s][q][t],  op = +1 add, -1 delete.
+ * Deleting a dimension with the same raw stream and R row it was built with
+ * restores the sketch without it (up to float32 rounding of S).
+ *   R_rows_host : float32 nd x k, HOST memory.
+ *   op_host     : int8 [nd], each +1 or -1, HOST memory.
+ *   S           : sketch from ts_sketch_build (same k, precision), updated in place.
+ *   stats       : output float64 [n_series][nd][2] for the listed dims; may be NULL.
+ *   dirty_host  : output uint8 [k] HOST memory, 1 for every sketch stream g that
+ *                 some row R_rows[q][g] != 0 touched (a count sketch touches one
+ *                 stream per dimension, a Gaussian R all k).  Re-profile those.
+ */
+TSK_API tsk_status ts_sketch_update_dims(tsk_ctx* ctx, void* S, const void* T_dims, int32_t t_dtype,
+                                         int32_t n_series, const int32_t* series_len_host, int32_t nd,
+                                         const float* R_rows_host, const int8_t* op_host, int32_t k,
+                                         int32_t precision, double* stats, uint8_t* dirty_host);
+
+/*
+ * mp_selfjoin - self-join matrix profile of every stream (Def. 6 with
+ * T_test = T_train; Def. 3 z-normalised Euclidean distance).
+ *
+ *   P[q][i] = min over j with |i - j| >= excl of dist(X_q[i:i+m], X_q[j:j+m])
+ *   I[q][i] = that j (-1, with P = +inf, when no j is admissible)
+ * dist(a, b) = || z(a) - z(b) ||, z with the population std; a constant window
+ * (variance <= 1e-12 * max(1, mean^2)) z-normalises to zeros, so two constant
+ * windows are at 0 and a constant and a non-constant one at sqrt(m).  Equal
+ * distances may resolve to any of the tied j.
+ *   X              : streams, stream layout, element type x_dtype.
+ *   stream_mask_host: uint8 [n_streams] HOST, 0 = skip the stream (outputs
+ *                     untouched); NULL = all.
+ *   excl           : exclusion half-width, 1 <= excl (ceil(m/4) is customary).
+ *   precision      : TSK_MP_FP32 (P float32) or TSK_MP_FP64 (P float64).
+ *   P, I           : outputs, stream layout (I int32).
+ * Requires 2 <= m <= 4096 and m <= len for every stream.
+ */
+TSK_API tsk_status mp_selfjoin(tsk_ctx* ctx, const void* X, int32_t x_dtype, int32_t n_streams,
+                               const int32_t* stream_len_host, const uint8_t* stream_mask_host, int32_t m,
+                               int32_t excl, int32_t precision, void* P, int32_t* I);
+
+/*
+ * discord_topk - aggregate over the streams of each series and rank the
+ * discords (Def. 5, Alg. 2 extended to a ranked list of K).
+ *
+ * Series s owns streams s*group .. s*group+group-1 of P/I (stream layout, all
+ * of length series_len_host[s], l = len - m + 1 profile entries):
+ *   A[i] = max_g P_g[i],  G[i] = the lowest g attaining it.
+ * Then K times: i* = argmax A (lowest i on ties), report
+ *   idx = i*, grp = G[i*], score = A[i*], nn = I_G[i*][i*]
+ * and exclude every i with |i - i*| < topk_excl.  When fewer than K indices
+ * remain the rest of the row is idx = grp = nn = -1, score = NaN.
+ *   P     : float32 (p_dtype TSK_F32) or float64 (TSK_F64).
+ *   outputs: device arrays [n_series][K]; score has P's element type.
+ */
+TSK_API tsk_status discord_topk(tsk_ctx* ctx, const void* P, int32_t p_dtype, const int32_t* I, int32_t n_series,
+                                const int32_t* series_len_host, int32_t group, int32_t m, int32_t K,
+                                int32_t topk_excl, int32_t* idx, int32_t* grp, void* score, int32_t* nn);
+
+/*
+ * mp_backward - adjoint of the ranked discord scores (not in the paper: the
+ * derivative of the definitions above, for attributing a discord to input
+ * dimensions).
+ *
+ * With the selections (idx, grp, nn) of discord_topk held fixed, the loss
+ *   L = sum_{s,r} dscore[s][r] * dist(S_s,g[i:i+m], S_s,g[j:j+m])
+ * is differentiated through the sketch and the global z-normalisation
+ * (bfloat16 rounding is treated as the identity):
+ *   d dist/dx = (rho x_hat - y_hat)/(sigma_x dist), d dist/dy = (rho y_hat - x_hat)/(sigma_y dist),
+ *   dT_bar = R dS, dR = sum_s T_bar dS^T,
+ *   dT_j = (dT_bar_j - mean(dT_bar_j) - T_bar_j mean(dT_bar_j T_bar_j)) / sigma_j.
+ * Entries with idx < 0, a constant window or dist = 0 contribute nothing.
+ *   dscore, idx, grp, nn : [n_series][K] (float32 / int32).
+ *   T, stats, R, S       : the forward's inputs and outputs (S float32).
+ *   dT                   : output float32, batch layout with d streams.
+ *   dR                   : output float32 d x k (summed over series).
+ */
+TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, const int32_t* idx, const int32_t* grp,
+                               const int32_t* nn, int32_t K, const void* T, int32_t t_dtype, const double* stats,
+                               const float* R, const float* S, int32_t n_series, const int32_t* series_len_host,
+                               int32_t d, int32_t k, int32_t m, float* dT, float* dR);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSKETCH_H */

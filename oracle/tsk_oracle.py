@@ -24,7 +24,7 @@ Readings where the paper is silent (the same readings the CUDA path takes):
   * exclusion: pairs with |i - j| < excl are trivial matches (excl = ceil(m/4)
     by default); a window with no admissible neighbour gets P = inf, I = -1.
   * sigma is the population standard deviation (ddof = 0), so that
-    dist^2 = 2 m (1 - rho).
+    dist^2 = 2 m (1 - rho).  A globally constant stream z-normalises to zeros.
   * a window is constant when its variance <= 1e-12 * max(1, mean^2); its
     z-normalised form is the zero vector, hence dist(const, const) = 0 and
     dist(const, non-const) = sqrt(m).
@@ -76,12 +76,16 @@ def bf16_round(x) -> np.ndarray:
 def global_znorm(T):
     """Per-stream z-normalisation over the whole length (Sec. III-A, T_bar).
 
-    T: (d, n).  Returns (T_bar, mu, sigma), sigma the population std.
+    T: (d, n).  Returns (T_bar, mu, sigma), sigma the population std.  A
+    stream that is constant over its whole length (sigma = 0) has no shape to
+    contribute and z-normalises to the zero stream.
     """
     T = np.asarray(T, dtype=np.float64)
     mu = T.mean(axis=1)
     sigma = np.sqrt(((T - mu[:, None]) ** 2).mean(axis=1))
-    Tbar = (T - mu[:, None]) / sigma[:, None]
+    Tbar = np.zeros_like(T)
+    live = sigma > 0
+    Tbar[live] = (T[live] - mu[live, None]) / sigma[live, None]
     return Tbar, mu, sigma
 
 
@@ -296,8 +300,10 @@ def grad_selected(T, R, selected, m: int, dscore=None) -> tuple:
         dS[g, j:j + m] += w * (rho * yh - xh) / (sy * dist)
     dTbar = R @ dS
     dR = Tbar @ dS.T
-    dT = (dTbar - dTbar.mean(axis=1, keepdims=True)
-          - Tbar * (dTbar * Tbar).mean(axis=1, keepdims=True)) / sigma[:, None]
+    dT = np.zeros_like(T)
+    live = sigma > 0
+    dT[live] = (dTbar[live] - dTbar[live].mean(axis=1, keepdims=True)
+                - Tbar[live] * (dTbar[live] * Tbar[live]).mean(axis=1, keepdims=True)) / sigma[live, None]
     return dT, dR
 
 

@@ -1,0 +1,273 @@
+"""Python face of libtsketch: the five C entry points with the same names, over
+torch CUDA tensors (torch supplies device memory and the current stream only;
+every step of the computation runs in the library's kernels).
+
+Layouts (see include/tsketch.h):
+  batch   T is a flat tensor holding n_series series packed back to back, each
+          (d, len_s) stream-major; `series_len` lists len_s.
+  streams X is a flat tensor of streams packed back to back; `stream_len`
+          lists their lengths.  P and I share X's packing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+_CTX: dict = {}
+
+
+def _ctx(device: torch.device):
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    h = _CTX.get(idx)
+    if h is None:
+        h = C.c_void_p()
+        N.check(N.lib().tsk_create(C.byref(h), idx, None), None, "tsk_create")
+        _CTX[idx] = h
+    N.check(N.lib().tsk_set_stream(h, C.c_void_p(torch.cuda.current_stream(idx).cuda_stream)), h, "tsk_set_stream")
+    return h
+
+
+def context(device=None):
+    """The library context used for `device` (created on first use)."""
+    return _ctx(torch.device("cuda", device) if isinstance(device, int) or device is None else torch.device(device))
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _i32_array(vals) -> C.Array:
+    a = np.ascontiguousarray(np.asarray(vals, dtype=np.int32))
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return N.TSK_F32
+    if t.dtype == torch.float64:
+        return N.TSK_F64
+    raise TypeError(f"series must be float32 or float64, got {t.dtype}")
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("arguments must be contiguous CUDA tensors")
+
+
+SKETCH_PRECISION = {"bf16": N.TSK_SKETCH_BF16, "fp32": N.TSK_SKETCH_FP32, "fp64": N.TSK_SKETCH_FP64}
+MP_PRECISION = {"fp32": N.TSK_MP_FP32, "fp64": N.TSK_MP_FP64}
+
+
+def default_excl(m: int) -> int:
+    return int(math.ceil(m / 4))
+
+
+def ts_sketch_build(T: torch.Tensor, R: torch.Tensor, series_len: Sequence[int], d: int,
+                    precision: str = "bf16", out: torch.Tensor | None = None,
+                    stats: torch.Tensor | None = None):
+    """Sketch S = R^T T_bar of every series (Sec. III-A, Alg. 1).
+
+    Returns (S, stats): S packed like T with k streams per series (float32, or
+    float64 for precision='fp64'); stats float64 (n_series, d, 2) = (mean, std).
+    """
+    _need_cuda(T, R)
+    k = int(R.shape[1])
+    ns = len(series_len)
+    sdt = torch.float64 if precision == "fp64" else torch.float32
+    total = int(sum(series_len))
+    if out is None:
+        out = torch.empty(k * total, dtype=sdt, device=T.device)
+    if stats is None:
+        stats = torch.empty((ns, d, 2), dtype=torch.float64, device=T.device)
+    Rf = R if R.dtype == torch.float32 else R.float().contiguous()
+    lens, lp = _i32_array(series_len)
+    h = _ctx(T.device)
+    N.check(N.lib().ts_sketch_build(h, _ptr(T), _dtype_code(T), ns, lp, d, _ptr(Rf), k,
+                                    SKETCH_PRECISION[precision], _ptr(out), _ptr(stats)), h, "ts_sketch_build")
+    return out, stats
+
+
+def ts_sketch_update_dims(S: torch.Tensor, T_dims: torch.Tensor, series_len: Sequence[int], R_rows,
+                          op: Sequence[int], precision: str = "bf16"):
+    """Add (op=+1) or delete (op=-1) dimensions of every series in S, in place (Sec. III-C).
+
+    R_rows: (nd, k) projection rows on the host.  Returns (dirty, stats): the
+    uint8 mask of sketch streams that changed, and the new dims' (mean, std).
+    """
+    _need_cuda(S, T_dims)
+    Rr = np.ascontiguousarray(np.asarray(R_rows.cpu() if isinstance(R_rows, torch.Tensor) else R_rows,
+                                         dtype=np.float32))
+    nd, k = Rr.shape
+    opa = np.ascontiguousarray(np.asarray(op, dtype=np.int8))
+    ns = len(series_len)
+    stats = torch.empty((ns, nd, 2), dtype=torch.float64, device=S.device)
+    dirty = np.zeros(k, dtype=np.uint8)
+    lens, lp = _i32_array(series_len)
+    h = _ctx(S.device)
+    N.check(N.lib().ts_sketch_update_dims(h, _ptr(S), _ptr(T_dims), _dtype_code(T_dims), ns, lp, nd,
+                                          Rr.ctypes.data_as(C.c_void_p), opa.ctypes.data_as(C.c_void_p), k,
+                                          SKETCH_PRECISION[precision], _ptr(stats),
+                                          dirty.ctypes.data_as(C.c_void_p)), h, "ts_sketch_update_dims")
+    return dirty, stats
+
+
+def mp_selfjoin(X: torch.Tensor, stream_len: Sequence[int], m: int, excl: int | None = None,
+                precision: str = "fp32", mask=None, P: torch.Tensor | None = None,
+                I: torch.Tensor | None = None):
+    """Self-join matrix profile of every stream (Def. 6).  Returns (P, I) packed like X."""
+    _need_cuda(X)
+    excl = default_excl(m) if excl is None else int(excl)
+    pdt = torch.float64 if precision == "fp64" else torch.float32
+    if P is None:
+        P = torch.empty(X.numel(), dtype=pdt, device=X.device)
+    if I is None:
+        I = torch.empty(X.numel(), dtype=torch.int32, device=X.device)
+    lens, lp = _i32_array(stream_len)
+    mk = None
+    mp = None
+    if mask is not None:
+        mk = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        mp = mk.ctypes.data_as(C.c_void_p)
+    h = _ctx(X.device)
+    N.check(N.lib().mp_selfjoin(h, _ptr(X), _dtype_code(X), len(stream_len), lp, mp, int(m), excl,
+                                MP_PRECISION[precision], _ptr(P), _ptr(I)), h, "mp_selfjoin")
+    return P, I
+
+
+def discord_topk(P: torch.Tensor, I: torch.Tensor, series_len: Sequence[int], group: int, m: int, K: int,
+                 topk_excl: int | None = None):
+    """Aggregate over each series' `group` streams and rank K discords (Def. 5, Alg. 2).
+
+    Returns (idx, grp, score, nn), each (n_series, K).
+    """
+    _need_cuda(P, I)
+    ns = len(series_len)
+    te = int(m) if topk_excl is None else int(topk_excl)
+    dev = P.device
+    idx = torch.empty((ns, K), dtype=torch.int32, device=dev)
+    grp = torch.empty((ns, K), dtype=torch.int32, device=dev)
+    nn = torch.empty((ns, K), dtype=torch.int32, device=dev)
+    score = torch.empty((ns, K), dtype=P.dtype, device=dev)
+    lens, lp = _i32_array(series_len)
+    h = _ctx(dev)
+    N.check(N.lib().discord_topk(h, _ptr(P), _dtype_code(P), _ptr(I), ns, lp, int(group), int(m), int(K), te,
+                                 _ptr(idx), _ptr(grp), _ptr(score), _ptr(nn)), h, "discord_topk")
+    return idx, grp, score, nn
+
+
+def mp_backward(dscore: torch.Tensor, idx, grp, nn, T: torch.Tensor, stats: torch.Tensor, R: torch.Tensor,
+                S: torch.Tensor, series_len: Sequence[int], d: int, m: int):
+    """Adjoint of the ranked discord scores: returns (dT packed like T, float32; dR (d, k))."""
+    _need_cuda(dscore, idx, grp, nn, T, stats, R, S)
+    k = int(R.shape[1])
+    ns = len(series_len)
+    K = int(idx.shape[1])
+    dT = torch.empty(T.numel(), dtype=torch.float32, device=T.device)
+    dR = torch.empty((d, k), dtype=torch.float32, device=T.device)
+    Rf = R if R.dtype == torch.float32 else R.float().contiguous()
+    lens, lp = _i32_array(series_len)
+    h = _ctx(T.device)
+    N.check(N.lib().mp_backward(h, _ptr(dscore), _ptr(idx), _ptr(grp), _ptr(nn), K, _ptr(T), _dtype_code(T),
+                                _ptr(stats), _ptr(Rf), _ptr(S), ns, lp, d, k, int(m), _ptr(dT), _ptr(dR)),
+            h, "mp_backward")
+    return dT, dR
+
+
+def sync(device=None, timeout_s: float = 0.0) -> None:
+    """Wait for the library's work on the current stream; raise on a device-side error."""
+    h = context(device)
+    N.check(N.lib().tsk_sync(h, float(timeout_s)), h, "tsk_sync")
+
+
+def launch_count(device=None) -> int:
+    """Kernels launched by the library on this device's context so far."""
+    return int(N.lib().tsk_launch_count(context(device)))
+
+
+def profile_enable(on: bool = True, device=None) -> None:
+    """Record CUDA events around the matrix-profile and sketch kernels."""
+    h = context(device)
+    N.check(N.lib().tsk_profile_enable(h, 1 if on else 0), h, "tsk_profile_enable")
+
+
+def profile_read(kernel: str = "mp_diag", device=None) -> tuple:
+    """(total device ms, launches) of `kernel` ('mp_diag' or 'sketch') since the last read."""
+    h = context(device)
+    ms = C.c_double()
+    n = C.c_int64()
+    kid = {"mp_diag": N.TSK_PROF_MP_DIAG, "sketch": N.TSK_PROF_SKETCH}[kernel]
+    N.check(N.lib().tsk_profile_read(h, kid, C.byref(ms), C.byref(n)), h, "tsk_profile_read")
+    return float(ms.value), int(n.value)
+
+
+def set_tile_rows(rows: int, device=None) -> None:
+    """Rows per matrix-profile work unit (multiple of 8)."""
+    h = context(device)
+    N.check(N.lib().tsk_set_tile_rows(h, int(rows)), h, "tsk_set_tile_rows")
+
+
+def reserve(nbytes: int, device=None) -> None:
+    h = context(device)
+    N.check(N.lib().tsk_reserve(h, int(nbytes)), h, "tsk_reserve")
+
+
+# ---------------------------------------------------------------------------
+# whole-pipeline helpers
+# ---------------------------------------------------------------------------
+
+def pack_batch(series) -> tuple:
+    """Pack a list of (d, len_s) arrays/tensors into one flat tensor + lengths (host-side layout)."""
+    lens = [int(s.shape[1]) for s in series]
+    flat = [torch.as_tensor(s).reshape(-1) for s in series]
+    return torch.cat(flat), lens
+
+
+def sketched_discords(T: torch.Tensor, R: torch.Tensor, series_len: Sequence[int], d: int, m: int, K: int,
+                      excl: int | None = None, topk_excl: int | None = None, sketch_precision: str = "bf16",
+                      mp_precision: str = "fp32"):
+    """Sketch, profile the k sketch streams, rank K discords per series (Alg. 1 then Alg. 2)."""
+    k = int(R.shape[1])
+    S, stats = ts_sketch_build(T, R, series_len, d, precision=sketch_precision)
+    slen = [n for n in series_len for _ in range(k)]
+    P, I = mp_selfjoin(S, slen, m, excl, precision=mp_precision)
+    idx, grp, score, nn = discord_topk(P, I, series_len, k, m, K, topk_excl)
+    return {"S": S, "stats": stats, "P": P, "I": I, "idx": idx, "grp": grp, "score": score, "nn": nn}
+
+
+def exact_discords(T: torch.Tensor, series_len: Sequence[int], d: int, m: int, K: int,
+                   excl: int | None = None, topk_excl: int | None = None, mp_precision: str = "fp32"):
+    """Exact multidimensional discords: one profile per raw dimension, max over d (Def. 5)."""
+    slen = [n for n in series_len for _ in range(d)]
+    P, I = mp_selfjoin(T, slen, m, excl, precision=mp_precision)
+    idx, grp, score, nn = discord_topk(P, I, series_len, d, m, K, topk_excl)
+    return {"P": P, "I": I, "idx": idx, "grp": grp, "score": score, "nn": nn}
+
+
+class DiscordScores(torch.autograd.Function):
+    """Top-K aggregated discord scores of the sketched path, differentiable in T and R.
+
+    forward(T, R, series_len, d, m, K) -> scores (n_series, K); backward uses
+    mp_backward with the forward's selections held fixed.
+    """
+
+    @staticmethod
+    def forward(ctx, T, R, series_len, d, m, K, excl=None, topk_excl=None, sketch_precision="fp32"):
+        res = sketched_discords(T, R, series_len, d, m, K, excl, topk_excl, sketch_precision=sketch_precision)
+        ctx.save_for_backward(T, R, res["stats"], res["S"], res["idx"], res["grp"], res["nn"])
+        ctx.meta = (list(series_len), d, m)
+        return res["score"].float()
+
+    @staticmethod
+    def backward(ctx, g):
+        T, R, stats, S, idx, grp, nn = ctx.saved_tensors
+        series_len, d, m = ctx.meta
+        S32 = S if S.dtype == torch.float32 else S.float().contiguous()
+        dT, dR = mp_backward(g.contiguous().float(), idx, grp, nn, T, stats, R, S32, series_len, d, m)
+        return dT.to(T.dtype), dR.to(R.dtype), None, None, None, None, None, None, None

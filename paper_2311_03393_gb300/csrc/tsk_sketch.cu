@@ -1,0 +1,297 @@
+// Global z-normalisation and the random-projection sketch S = R^T T_bar
+// (Sec. III-A, Alg. 1), plus dimension addition/deletion (Sec. III-C).
+//
+// The sketch is a dense contraction over d with a tiny output width k; it is
+// bound by reading T once.  In bfloat16 mode each element of T is normalised
+// in float64, rounded to bfloat16 (nearest even) and fed to the tensor cores;
+// products are summed in float32.
+#include "tsk_internal.cuh"
+
+#include <cmath>
+
+namespace {
+
+constexpr int kStatThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Column statistics: mean and population std of every stream, float64.
+// Sums are taken of x - x[0] (a shift that keeps them well conditioned).
+// ---------------------------------------------------------------------------
+template <typename TIn>
+__global__ void __launch_bounds__(kStatThreads) k_colstats(const TIn* __restrict__ T, const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ len, double* __restrict__ stats,
+                                                           int* __restrict__ err) {
+  const int64_t q = blockIdx.x;
+  const int64_t base = off[q];
+  const int n = len[q];
+  const double x0 = tsk_ld(T, base);
+  double s1 = 0.0, s2 = 0.0;
+  bool bad = false;
+  for (int t = threadIdx.x; t < n; t += kStatThreads) {
+    const double x = tsk_ld(T, base + t);
+    bad |= !isfinite(x);
+    const double y = x - x0;
+    s1 += y;
+    s2 = fma(y, y, s2);
+  }
+  if (bad) atomicOr(err, TSK_DEVERR_NONFINITE);
+  __shared__ double r1[kStatThreads / 32], r2[kStatThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(TSK_FULL_MASK, s1, o);
+    s2 += __shfl_xor_sync(TSK_FULL_MASK, s2, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { r1[w] = s1; r2[w] = s2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int u = 0; u < kStatThreads / 32; ++u) { a += r1[u]; b += r2[u]; }
+    const double mean_y = a / n;
+    const double var = fmax(0.0, b / n - mean_y * mean_y);
+    stats[2 * q + 0] = x0 + mean_y;
+    stats[2 * q + 1] = sqrt(var);
+  }
+}
+
+// Normalised element in float64: (x - mu) / sigma, 0 for a constant stream.
+__device__ __forceinline__ double tsk_tbar(double x, double mu, double rinv) { return (x - mu) * rinv; }
+
+// ---------------------------------------------------------------------------
+// bfloat16 tensor-core sketch.  One CTA = 64 time points of one series x all
+// k outputs; 4 warps, one m16 tile each, ceil(k/8) n8 tiles; K = d in chunks
+// of 16 staged through shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kSkT = 64;       // time points per CTA
+constexpr int kSkThreads = 128;
+constexpr int kSkPad = 24;     // padded row of 16 bf16 (conflict-free fragment loads)
+
+template <typename TIn>
+__global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restrict__ T, const int64_t* __restrict__ cum,
+                                                           const int32_t* __restrict__ len,
+                                                           const int64_t* __restrict__ blk_prefix, int32_t n_series,
+                                                           int32_t d, const float* __restrict__ R, int32_t k,
+                                                           const double* __restrict__ stats, float* __restrict__ S) {
+  __shared__ __align__(16) uint16_t As[kSkT][kSkPad];
+  __shared__ __align__(16) uint16_t Bs[64][kSkPad];
+  __shared__ double smu[16], srinv[16];
+
+  const int s = tsk_find_segment<int64_t>(blk_prefix, n_series, static_cast<int64_t>(blockIdx.x));
+  const int n = len[s];
+  const int t0 = static_cast<int>(blockIdx.x - blk_prefix[s]) * kSkT;
+  const int64_t tbase = static_cast<int64_t>(d) * cum[s];
+  const int64_t sbase = static_cast<int64_t>(k) * cum[s];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int NT = (k + 7) >> 3;
+
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.f;
+
+  for (int j0 = 0; j0 < d; j0 += 16) {
+    if (tid < 16) {
+      const int j = j0 + tid;
+      double mu = 0.0, ri = 0.0;
+      if (j < d) {
+        mu = stats[2 * (static_cast<int64_t>(s) * d + j) + 0];
+        const double sg = stats[2 * (static_cast<int64_t>(s) * d + j) + 1];
+        ri = sg > 0.0 ? 1.0 / sg : 0.0;
+      }
+      smu[tid] = mu;
+      srinv[tid] = ri;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < (16 * kSkT) / kSkThreads; ++u) {
+      const int e = tid + u * kSkThreads;
+      const int jl = e / kSkT, tl = e % kSkT;
+      const int j = j0 + jl, t = t0 + tl;
+      uint16_t h = 0;
+      if (j < d && t < n) h = tsk_f64_to_bf16_bits(tsk_tbar(tsk_ld(T, tbase + static_cast<int64_t>(j) * n + t), smu[jl], srinv[jl]));
+      As[tl][jl] = h;
+    }
+    for (int e = tid; e < 16 * NT * 8; e += kSkThreads) {
+      const int g = e / 16, jl = e % 16;
+      const int j = j0 + jl;
+      uint16_t h = 0;
+      if (j < d && g < k) h = tsk_f64_to_bf16_bits(static_cast<double>(R[static_cast<int64_t>(j) * k + g]));
+      Bs[g][jl] = h;
+    }
+    __syncthreads();
+    const int r = warp * 16 + gid;
+    const uint32_t a0 = *reinterpret_cast<const uint32_t*>(&As[r][2 * tig]);
+    const uint32_t a1 = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * tig]);
+    const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&As[r][2 * tig + 8]);
+    const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * tig + 8]);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      if (nt < NT) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][2 * tig]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][2 * tig + 8]);
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    if (nt < NT) {
+      const int g = nt * 8 + 2 * tig;
+      const int t = t0 + warp * 16 + gid;
+      if (t < n) {
+        if (g < k) S[sbase + static_cast<int64_t>(g) * n + t] = acc[nt][0];
+        if (g + 1 < k) S[sbase + static_cast<int64_t>(g + 1) * n + t] = acc[nt][1];
+      }
+      if (t + 8 < n) {
+        if (g < k) S[sbase + static_cast<int64_t>(g) * n + t + 8] = acc[nt][2];
+        if (g + 1 < k) S[sbase + static_cast<int64_t>(g + 1) * n + t + 8] = acc[nt][3];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// float32 / float64 sketch on the FMA pipes (one thread per time point).
+// ---------------------------------------------------------------------------
+template <typename TIn, typename Acc>
+__global__ void __launch_bounds__(128) k_sketch_fma(const TIn* __restrict__ T, const int64_t* __restrict__ cum,
+                                                    const int32_t* __restrict__ len,
+                                                    const int64_t* __restrict__ blk_prefix, int32_t n_series,
+                                                    int32_t d, const float* __restrict__ R, int32_t k,
+                                                    const double* __restrict__ stats, Acc* __restrict__ S) {
+  const int s = tsk_find_segment<int64_t>(blk_prefix, n_series, static_cast<int64_t>(blockIdx.x));
+  const int n = len[s];
+  const int t = static_cast<int>(blockIdx.x - blk_prefix[s]) * kSkT + static_cast<int>(threadIdx.x);
+  if (threadIdx.x >= kSkT || t >= n) return;
+  const int64_t tbase = static_cast<int64_t>(d) * cum[s];
+  const int64_t sbase = static_cast<int64_t>(k) * cum[s];
+  for (int g0 = 0; g0 < k; g0 += 8) {
+    Acc acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = Acc(0);
+    for (int j = 0; j < d; ++j) {
+      const double mu = stats[2 * (static_cast<int64_t>(s) * d + j) + 0];
+      const double sg = stats[2 * (static_cast<int64_t>(s) * d + j) + 1];
+      const double ri = sg > 0.0 ? 1.0 / sg : 0.0;
+      const Acc x = static_cast<Acc>(tsk_tbar(tsk_ld(T, tbase + static_cast<int64_t>(j) * n + t), mu, ri));
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (g0 + u < k) acc[u] = fma(static_cast<Acc>(R[static_cast<int64_t>(j) * k + g0 + u]), x, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (g0 + u < k) S[sbase + static_cast<int64_t>(g0 + u) * n + t] = acc[u];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rank-one updates S += op_q r_q T_bar_q (Sec. III-C); one thread per sample.
+// ---------------------------------------------------------------------------
+template <typename TIn, typename Acc>
+__global__ void k_update_dims(Acc* __restrict__ S, const TIn* __restrict__ Td, const int64_t* __restrict__ cum,
+                              const int32_t* __restrict__ len, int32_t n_series, int64_t total, int32_t nd,
+                              const float* __restrict__ Rrows, const int8_t* __restrict__ op, int32_t k,
+                              int32_t precision, const double* __restrict__ stats) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int s = tsk_find_segment<int64_t>(cum, n_series, e);
+  const int n = len[s];
+  const int t = static_cast<int>(e - cum[s]);
+  const int64_t dbase = static_cast<int64_t>(nd) * cum[s];
+  const int64_t sbase = static_cast<int64_t>(k) * cum[s];
+  for (int q = 0; q < nd; ++q) {
+    const double mu = stats[2 * (static_cast<int64_t>(s) * nd + q) + 0];
+    const double sg = stats[2 * (static_cast<int64_t>(s) * nd + q) + 1];
+    const double ri = sg > 0.0 ? 1.0 / sg : 0.0;
+    const double tb = tsk_tbar(tsk_ld(Td, dbase + static_cast<int64_t>(q) * n + t), mu, ri);
+    const Acc sign = static_cast<Acc>(op[q]);
+    if (precision == TSK_SKETCH_BF16) {
+      const float x = tsk_bf16_bits_to_f32(tsk_f64_to_bf16_bits(tb));
+      for (int g = 0; g < k; ++g) {
+        const float r = tsk_bf16_bits_to_f32(tsk_f64_to_bf16_bits(static_cast<double>(Rrows[q * k + g])));
+        if (r != 0.f) S[sbase + static_cast<int64_t>(g) * n + t] += sign * static_cast<Acc>(r * x);
+      }
+    } else {
+      const Acc x = static_cast<Acc>(tb);
+      for (int g = 0; g < k; ++g) {
+        const Acc r = static_cast<Acc>(Rrows[q * k + g]);
+        if (r != Acc(0)) S[sbase + static_cast<int64_t>(g) * n + t] = fma(sign * r, x, S[sbase + static_cast<int64_t>(g) * n + t]);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+tsk_status tsk_launch_colstats(tsk_ctx* ctx, const void* T, int t_dtype, const int64_t* d_off, const int32_t* d_len,
+                               int64_t n_streams, double* stats) {
+  if (n_streams <= 0) return TSK_OK;
+  if (n_streams > 0x7fffffff) return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "too many streams");
+  const dim3 grid(static_cast<unsigned>(n_streams));
+  if (t_dtype == TSK_F64)
+    k_colstats<double><<<grid, kStatThreads, 0, ctx->stream>>>(static_cast<const double*>(T), d_off, d_len, stats, ctx->d_err);
+  else
+    k_colstats<float><<<grid, kStatThreads, 0, ctx->stream>>>(static_cast<const float*>(T), d_off, d_len, stats, ctx->d_err);
+  TSK_LAUNCH_CHECK(ctx, "k_colstats");
+  return TSK_OK;
+}
+
+tsk_status tsk_launch_sketch(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_series, const int64_t* d_cum,
+                             const int32_t* d_len, const int64_t* d_blk_prefix, int64_t total_blocks, int32_t d,
+                             const float* R, int32_t k, int32_t precision, const double* stats, void* S,
+                             int64_t /*max_len*/) {
+  if (total_blocks <= 0) return TSK_OK;
+  if (total_blocks > 0x7fffffff) return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "batch too large");
+  const dim3 grid(static_cast<unsigned>(total_blocks));
+  const bool f64in = t_dtype == TSK_F64;
+  tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
+  if (precision == TSK_SKETCH_BF16) {
+    if (f64in)
+      k_sketch_bf16<double><<<grid, kSkThreads, 0, ctx->stream>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
+    else
+      k_sketch_bf16<float><<<grid, kSkThreads, 0, ctx->stream>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
+    TSK_LAUNCH_CHECK(ctx, "k_sketch_bf16");
+  } else if (precision == TSK_SKETCH_FP32) {
+    if (f64in)
+      k_sketch_fma<double, float><<<grid, 128, 0, ctx->stream>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
+    else
+      k_sketch_fma<float, float><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
+    TSK_LAUNCH_CHECK(ctx, "k_sketch_fma<f32>");
+  } else {
+    if (f64in)
+      k_sketch_fma<double, double><<<grid, 128, 0, ctx->stream>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<double*>(S));
+    else
+      k_sketch_fma<float, double><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<double*>(S));
+    TSK_LAUNCH_CHECK(ctx, "k_sketch_fma<f64>");
+  }
+  return TSK_OK;
+}
+
+tsk_status tsk_launch_update_dims(tsk_ctx* ctx, void* S, const void* T_dims, int t_dtype, int32_t n_series,
+                                  const int64_t* d_cum, const int32_t* d_len, int64_t total_samples, int32_t nd,
+                                  const float* d_Rrows, const int8_t* d_op, int32_t k, int32_t precision,
+                                  const double* stats) {
+  if (total_samples <= 0) return TSK_OK;
+  const int threads = 256;
+  const int64_t blocks = (total_samples + threads - 1) / threads;
+  if (blocks > 0x7fffffff) return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "batch too large");
+  const bool f64in = t_dtype == TSK_F64;
+  if (precision == TSK_SKETCH_FP64) {
+    if (f64in)
+      k_update_dims<double, double><<<static_cast<unsigned>(blocks), threads, 0, ctx->stream>>>(static_cast<double*>(S), static_cast<const double*>(T_dims), d_cum, d_len, n_series, total_samples, nd, d_Rrows, d_op, k, precision, stats);
+    else
+      k_update_dims<float, double><<<static_cast<unsigned>(blocks), threads, 0, ctx->stream>>>(static_cast<double*>(S), static_cast<const float*>(T_dims), d_cum, d_len, n_series, total_samples, nd, d_Rrows, d_op, k, precision, stats);
+  } else {
+    if (f64in)
+      k_update_dims<double, float><<<static_cast<unsigned>(blocks), threads, 0, ctx->stream>>>(static_cast<float*>(S), static_cast<const double*>(T_dims), d_cum, d_len, n_series, total_samples, nd, d_Rrows, d_op, k, precision, stats);
+    else
+      k_update_dims<float, float><<<static_cast<unsigned>(blocks), threads, 0, ctx->stream>>>(static_cast<float*>(S), static_cast<const float*>(T_dims), d_cum, d_len, n_series, total_samples, nd, d_Rrows, d_op, k, precision, stats);
+  }
+  TSK_LAUNCH_CHECK(ctx, "k_update_dims");
+  return TSK_OK;
+}

@@ -145,6 +145,16 @@ def test_global_znorm_matches_scipy_zscore():
     np.testing.assert_allclose(sigma, np.std(T, axis=1), rtol=1e-12)
 
 
+def test_globally_constant_stream_contributes_nothing():
+    """A constant stream has no shape: the sketch of the other streams is unchanged by it."""
+    T, _ = synth.random_walks(4, 300, 20, 0, seed=19, dtype=np.float64)
+    Tc = np.vstack([T, np.full((1, 300), 7.5)])
+    R = synth.gaussian_R(5, 2, 20).astype(np.float64)
+    Tbar, _, sigma = o.global_znorm(Tc)
+    assert sigma[4] == 0 and np.all(Tbar[4] == 0)
+    np.testing.assert_allclose(o.sketch(Tbar, R), o.sketch(o.global_znorm(T)[0], R[:4]), rtol=0, atol=1e-12)
+
+
 def test_fig1_sum_of_streams_is_the_k1_sketch_and_keeps_the_discord():
     """Fig. 1: the MP of the sum of z-normalised streams still shows a discord of one stream."""
     n, m = 1200, 60
