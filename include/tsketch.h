@@ -98,9 +98,10 @@ TSK_API tsk_status tsk_mp_workspace_bytes(tsk_ctx* ctx, int32_t n_streams, const
  * then read and clear the device error word.  TSK_ERR_TIMEOUT if the deadline
  * passed (the work keeps running; call again). */
 TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s);
-/* Rows per matrix-profile work unit (a band of diagonals x `rows` rows);
- * a multiple of 8 in [8, 1 << 20].  Smaller units balance short streams,
- * larger ones amortise the float64 anchors.  Default 2048. */
+/* Rows per matrix-profile work unit (a band of 512 diagonals x `rows` rows):
+ * 0 = automatic (about 64 units per resident warp, 1024..8192), else a
+ * multiple of 32 in [32, 1 << 20].  Smaller units balance short streams,
+ * larger ones amortise the float64 anchors. */
 TSK_API tsk_status tsk_set_tile_rows(tsk_ctx* ctx, int32_t rows);
 /* Number of kernels this context has launched since creation. */
 TSK_API int64_t tsk_launch_count(const tsk_ctx* ctx);

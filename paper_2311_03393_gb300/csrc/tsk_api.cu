@@ -10,6 +10,7 @@
 
 int tsk_mp_pad();
 int tsk_mp_chunk();
+int tsk_mp_chunk_rows();
 
 namespace {
 
@@ -162,21 +163,40 @@ tsk_status batch_layout(tsk_ctx* ctx, int32_t n_series, const int32_t* lens, int
 
 tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* mask, int32_t m, int32_t excl,
                    int32_t prec, tsk_mp_plan* plan) {
-  const int32_t H = ctx->mp_H;
   const int32_t D = tsk_mp_band_width();
+  int32_t H = ctx->mp_H;
+  if (H <= 0) {
+    // rows per work unit: about 64 units per resident warp, within [1024, 8192]
+    // (warps claim runs of consecutive units, so small units cost few anchors)
+    double cells = 0.0;
+    for (int q = 0; q < n; ++q) {
+      if (mask && !mask[q]) continue;
+      const double e = static_cast<double>(lens[q]) - m + 1 - excl;
+      if (e > 0) cells += e * (e + 1) / 2;
+    }
+    const double warps = static_cast<double>(ctx->sm_count) * 12.0;
+    const double rows = cells / (warps * 64.0 * D);
+    const int32_t step = tsk_mp_chunk_rows();
+    H = static_cast<int32_t>(std::min(8192.0, std::max(1024.0, rows)));
+    H = (H + step - 1) / step * step;
+  }
   std::string key = "mp";
   const int32_t hdr[6] = {n, m, excl, prec, H, D};
   append(key, hdr, 6);
   append(key, lens, n);
   if (mask) append(key, mask, n);
   tsk_status st = TSK_OK;
+  bool ntiles_overflow = false;
   const int pad = tsk_mp_pad();
   const int chunk = tsk_mp_chunk();
   const Blob* b = blob_get(ctx, key, [&](std::vector<char>& buf, std::vector<int64_t>& meta) {
-    std::vector<int64_t> xoff(n + 1, 0), woff(n + 1, 0), chp(n + 1, 0), tp(n + 1, 0), boff(n + 1, 0);
-    std::vector<int32_t> len(lens, lens + n), bp;
+    std::vector<int64_t> xoff(n + 1, 0), woff(n + 1, 0), chp(n + 1, 0), tp(n + 1, 0);
+    std::vector<int32_t> len(lens, lens + n);
     std::vector<uint8_t> sm(n, 1);
-    const int32_t excl4 = excl & ~3;
+    // float32 path: interior tiles of every band first, then the triangular ends
+    // (the last rows of a band, where its diagonals run out, need masking)
+    std::vector<int32_t> tiles_int, tiles_tri;
+    const int32_t chunk_rows = tsk_mp_chunk_rows();
     for (int q = 0; q < n; ++q) {
       const bool on = !mask || mask[q];
       sm[q] = on ? 1 : 0;
@@ -184,27 +204,29 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
       xoff[q + 1] = xoff[q] + lens[q];
       woff[q + 1] = woff[q] + ((l + pad + 3) & ~int64_t(3));
       chp[q + 1] = chp[q] + (on ? (l + chunk - 1) / chunk : 0);
-      int64_t tiles = 0;
-      if (prec == TSK_MP_FP64) {
-        tiles = on ? std::max<int64_t>(0, l - excl) : 0;
-        bp.push_back(0);
-      } else {
-        const int64_t nb = (on && l > excl) ? (l - excl4 + D - 1) / D : 0;
-        bp.push_back(0);
-        for (int64_t bb = 0; bb < nb; ++bb) {
-          const int64_t dmin = std::max<int64_t>(excl, excl4 + bb * D);
-          const int64_t rows = std::max<int64_t>(0, l - dmin);
-          tiles += (rows + H - 1) / H;
-          bp.push_back(static_cast<int32_t>(tiles));
+      tp[q + 1] = tp[q] + ((on && prec == TSK_MP_FP64) ? std::max<int64_t>(0, l - excl) : 0);
+      if (!on || prec == TSK_MP_FP64 || l <= excl) continue;
+      for (int64_t d0 = excl; d0 < l; d0 += D) {
+        const int64_t rows = l - d0;                       // rows with at least one cell
+        int64_t rint = std::max<int64_t>(0, rows - (D - 1));  // rows with all D diagonals
+        rint -= rint % chunk_rows;
+        for (int64_t r0 = 0; r0 < rint; r0 += H) {
+          const int64_t r1 = std::min<int64_t>(r0 + H, rint);
+          tiles_int.insert(tiles_int.end(), {q, static_cast<int32_t>(d0), static_cast<int32_t>(r0),
+                                             static_cast<int32_t>(r1)});
         }
+        if (rows > rint)
+          tiles_tri.insert(tiles_tri.end(), {q, static_cast<int32_t>(d0), static_cast<int32_t>(rint),
+                                             static_cast<int32_t>(static_cast<uint32_t>(rows) | 0x80000000u)});
       }
-      boff[q + 1] = static_cast<int64_t>(bp.size());
-      tp[q + 1] = tp[q] + tiles;
     }
-    meta.assign(12, 0);
+    tiles_int.insert(tiles_int.end(), tiles_tri.begin(), tiles_tri.end());
+    const int64_t ntiles = prec == TSK_MP_FP64 ? tp[n] : static_cast<int64_t>(tiles_int.size() / 4);
+    if (ntiles > 0x7fffffffLL) ntiles_overflow = true;
+    meta.assign(11, 0);
     meta[0] = woff[n];
     meta[1] = chp[n];
-    meta[2] = tp[n];
+    meta[2] = ntiles;
     meta[3] = xoff[n];
     meta[4] = static_cast<int64_t>(put(buf, xoff));
     meta[5] = static_cast<int64_t>(put(buf, len));
@@ -212,10 +234,11 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
     meta[7] = static_cast<int64_t>(put(buf, woff));
     meta[8] = static_cast<int64_t>(put(buf, chp));
     meta[9] = static_cast<int64_t>(put(buf, tp));
-    meta[10] = static_cast<int64_t>(put(buf, boff));
-    meta[11] = static_cast<int64_t>(put(buf, bp));
+    meta[10] = static_cast<int64_t>(put(buf, tiles_int));
   }, &st);
   if (!b) return st;
+  if (ntiles_overflow || b->meta[2] > 0x7fffffffLL)
+    return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "mp_selfjoin: more than 2^31 work units; raise tsk_set_tile_rows");
   char* base = static_cast<char*>(b->dev);
   plan->m = m;
   plan->excl = excl;
@@ -232,8 +255,7 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
   plan->woff = reinterpret_cast<int64_t*>(base + b->meta[7]);
   plan->chunk_prefix = reinterpret_cast<int64_t*>(base + b->meta[8]);
   plan->tile_prefix = reinterpret_cast<int64_t*>(base + b->meta[9]);
-  plan->band_off = reinterpret_cast<int64_t*>(base + b->meta[10]);
-  plan->band_prefix = reinterpret_cast<int32_t*>(base + b->meta[11]);
+  plan->tiles = reinterpret_cast<int4*>(base + b->meta[10]);
   return TSK_OK;
 }
 
@@ -402,8 +424,8 @@ extern "C" TSK_API tsk_status tsk_profile_read(tsk_ctx* ctx, int32_t kernel, dou
 
 extern "C" TSK_API tsk_status tsk_set_tile_rows(tsk_ctx* ctx, int32_t rows) {
   if (!ctx) return TSK_ERR_INVALID_ARG;
-  if (rows < 8 || rows > (1 << 20) || rows % 8 != 0)
-    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "tsk_set_tile_rows: rows must be a multiple of 8 in [8, 2^20]");
+  if (rows != 0 && (rows < 32 || rows > (1 << 20) || rows % 32 != 0))
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "tsk_set_tile_rows: rows must be 0 (automatic) or a multiple of 32 in [32, 2^20]");
   ctx->mp_H = rows;
   return TSK_OK;
 }

@@ -33,9 +33,8 @@ struct tsk_mp_plan {
   uint8_t* smask = nullptr;        // [n]
   int64_t* woff = nullptr;         // [n+1] window-array offsets
   int64_t* chunk_prefix = nullptr; // [n+1] window-stat chunks
-  int64_t* tile_prefix = nullptr;  // [n+1] matrix-profile work units
-  int64_t* band_off = nullptr;     // [n+1] offset of each stream's band prefix
-  int32_t* band_prefix = nullptr;  // [sum(nb)+n] tiles before band b
+  int64_t* tile_prefix = nullptr;  // [n+1] float64 path: diagonals before each stream
+  int4* tiles = nullptr;           // float32 path work list {stream, d0, r0, r1 | masked << 31}
   // host summaries
   int64_t total_windows = 0;  // sum of (l + pad) over streams
   int64_t total_chunks = 0;
@@ -52,7 +51,7 @@ struct tsk_ctx {
   int* d_err = nullptr;                 // device error word
   std::string last_error;
   int64_t launches = 0;
-  int mp_H = 2048;                      // rows per matrix-profile work unit
+  int mp_H = 0;                         // rows per matrix-profile work unit (0 = automatic)
   bool prof = false;                    // record events around the timed kernels
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[TSK_PROF_COUNT];
 };

@@ -35,13 +35,18 @@
 
 namespace {
 
-constexpr int kV = 8;                    // diagonals per lane
+constexpr int kVh = 8;                   // diagonals per lane in each half band
+constexpr int kHalf = 32 * kVh;          // 256 diagonals per half band
+constexpr int kBand = 2 * kHalf;         // 512 diagonals per warp band
+constexpr int kChunk = 32;               // rows between row flushes / ring refills
+constexpr int kRingEntries = 384;        // column ring entries of (half a, half b) pairs (multiple of 128)
+constexpr int kRingInit = 288;           // entries filled before the first row
 constexpr int kWarps = 4;                // warps per CTA
-constexpr int kD = 32 * kV;              // diagonals per band
-constexpr int kTagIn = 15;               // tag of a column maximum inherited from another lane
+constexpr int kMaxClaim = 16;            // work units a warp claims at once (at most)
+constexpr int kMaxWalk = 16384;          // rows walked from one float64 anchor (at most)
 constexpr int kWinChunk = 1024;          // windows per window-stats CTA
 constexpr int kWinThreads = 256;
-constexpr int kPad = kD + 4 * kV + 64;   // zeroed slack after each stream's window arrays
+constexpr int kPad = 2048;               // zeroed slack after each stream's window arrays
 constexpr float kEmpty = -3.0f;          // below every correlation
 constexpr double kConstRelVar = 1e-12;
 
@@ -198,196 +203,333 @@ __global__ void __launch_bounds__(kWinThreads) k_next_const(const int32_t* __res
 
 // ---------------------------------------------------------------------------
 // 3. the diagonal kernel (float32 recurrence)
+//
+// A warp owns a band of 512 diagonals d0 .. d0+511 and a block of rows.  Lane
+// t walks two groups of 8 diagonals, d0 + 8t + v (half a) and the same + 256
+// (half b); the two halves advance in lockstep, so every quantity of a cell
+// comes as a float2 pair (half a, half b) and the arithmetic runs as paired
+// float32 FMA/MUL.  Per row the lane's 8 + 8 cells update
+//   - the row maximum (one key per half, reduced over lanes in shared memory
+//     every 32 rows), and
+//   - 8 + 8 column maxima held in registers; as the rows advance the band's
+//     columns slide, the column leaving lane t passes to lane t-1 and the one
+//     leaving lane 0 is complete for this band.
+// A key is the correlation with its 8 low mantissa bits replaced by the
+// diagonal's offset within its half (8t + v), so maxima carry their argmax.
+// Column data (df, dg, 1/norm) stream through a swizzled shared-memory ring
+// refilled 32 rows ahead; row data through a 32-row buffer of broadcast pairs.
 // ---------------------------------------------------------------------------
 struct MpArgs {
   const void* X;
   const int64_t* xoff;
   const int32_t* len;
   const int64_t* woff;
-  const int64_t* tile_prefix;
-  const int64_t* band_off;
-  const int32_t* band_prefix;
+  const int64_t* tile_prefix;  // float64 path: diagonals before stream q
+  const int4* tiles;           // float32 path: {stream, d0, r0, r1 | masked << 31}
   unsigned long long* counter;
   WinArrays wa;
   int64_t total_tiles;
-  int n_streams, m, excl, excl4, H;
+  int n_streams, m, excl, H;
+  int total_warps;
 };
 
-__device__ __forceinline__ float tag_key(float rho, unsigned tag) {
-  return __uint_as_float((__float_as_uint(rho) & ~15u) | tag);
-}
-__device__ __forceinline__ float untag_key(float key) { return __uint_as_float(__float_as_uint(key) & ~15u); }
+struct __align__(16) MpWarpSmem {
+  float2 ring[3][kRingEntries];  // column pairs (half a, half b), swizzled slots
+  float4 rrow[2][3][kChunk / 2]; // row broadcast pairs (v_s, v_s, v_s+1, v_s+1), double buffered
+  float2 rowbuf[kChunk][32];     // (row key half a, half b): [step][lane ^ (step & 15)]
+  float2 colbuf[kChunk];         // keys of the columns leaving lane 0, per step
+};
 
-// Merge the buffered rows/columns of `count` steps into the global profile.
-// Slot u of the buffers belongs to row `base + u` (and to column base + u + d0,
-// the column that left lane 0 at that step).
-template <int V>
-__device__ __forceinline__ void flush_rows_cols(float (*rowbuf)[33], const float* cbk, const int* cbr, int count, int base,
-                                                int d0, int l, unsigned long long* best, int lane) {
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ float tag_key(float rho, unsigned tag) {
+  return __uint_as_float((__float_as_uint(rho) & 0xffffff00u) | tag);
+}
+__device__ __forceinline__ float untag_key(float key) { return __uint_as_float(__float_as_uint(key) & 0xffffff00u); }
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+// ring slot (0 <= e < kRingEntries) -> physical 8-byte slot.  At a step the lanes
+// read entries e0 + 8t; XOR of the low three bits with bits 4..6 spreads the 16
+// lanes of a half warp over 16 distinct 8-byte bank pairs (the ring size is a
+// multiple of 128 entries, so the pattern continues across its wrap).
+__device__ __forceinline__ int ring_phys(int e) { return e ^ ((e >> 4) & 7); }
+
+template <typename TX>
+__device__ __forceinline__ double ld_guard(const TX* __restrict__ x, int idx, int n) {
+  return idx < n ? static_cast<double>(x[idx]) : 0.0;
+}
+
+// Merge the 32 (or `count`) buffered rows and lane-0 column exits into the profile.
+// Buffer slot u belongs to row base + u and to columns base + u + d0 (+ 256).
+__device__ __forceinline__ void flush_chunk(MpWarpSmem& w, int count, int base, int d0, int l,
+                                            unsigned long long* __restrict__ best, int lane) {
   __syncwarp();
   if (lane < count) {
     const int ir = base + lane;
-    float bk = kEmpty;
-    int bl = 0;
-#pragma unroll 8
-    for (int u = 0; u < 32; ++u) {
-      const float kk = rowbuf[lane][u];
-      if (kk > bk) { bk = kk; bl = u; }
+    float ma = kEmpty, mb = kEmpty;
+    const int sw = lane & 15;
+#pragma unroll
+    for (int u = 0; u < 32; u += 2) {
+      const float2 q0 = w.rowbuf[lane][u ^ sw], q1 = w.rowbuf[lane][(u + 1) ^ sw];
+      ma = max3f(ma, q0.x, q1.x);
+      mb = max3f(mb, q0.y, q1.y);
     }
+    const bool useb = mb > ma;
+    const float bk = useb ? mb : ma;
     if (bk > -2.f) {
-      const int col = ir + d0 + bl * V + static_cast<int>(__float_as_uint(bk) & 15u);
+      const int col = ir + d0 + (useb ? kHalf : 0) + static_cast<int>(__float_as_uint(bk) & 0xffu);
       atomicMax(&best[ir], tsk_pack(untag_key(bk), col));
     }
-    const float ck = cbk[lane];
-    const int jc = ir + d0;
-    if (ck > -2.f && jc < l) atomicMax(&best[jc], tsk_pack(untag_key(ck), cbr[lane]));
+    const float2 ck = w.colbuf[lane];
+    const int ja = ir + d0;
+    if (ck.x > -2.f && ja < l)
+      atomicMax(&best[ja], tsk_pack(untag_key(ck.x), ir - static_cast<int>(__float_as_uint(ck.x) & 0xffu)));
+    if (ck.y > -2.f && ja + kHalf < l)
+      atomicMax(&best[ja + kHalf], tsk_pack(untag_key(ck.y), ir - static_cast<int>(__float_as_uint(ck.y) & 0xffu)));
   }
   __syncwarp();
 }
 
-template <int V, bool MASKED, typename TX>
-__device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ x, int n, int l, int64_t wb, int d0, int r0,
-                                        int rEnd, float (*rowbuf)[33], float* cbk, int* cbr, int lane) {
-  const double* __restrict__ mu = a.wa.mu + wb;
+template <bool MASKED, typename TX>
+__device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ x, int n, int l, int64_t wb, int d0,
+                                        int r0, int rEnd, MpWarpSmem& w, int lane) {
   const float* __restrict__ inv = a.wa.inv + wb;
   const float* __restrict__ df = a.wa.df + wb;
   const float* __restrict__ dg = a.wa.dg + wb;
   unsigned long long* __restrict__ best = a.wa.best + wb;
-  const int dl = d0 + lane * V;
   const int m = a.m;
+  const int dA = d0 + lane * kVh;  // first diagonal of half a (half b: + kHalf)
 
-  // exact anchors c(r0, r0 + dl + v) in float64: sum_t (x[r0+t] - mean_r0) x[c+t]
-  float cov[V];
+  // ---- exact anchors c(r0, r0 + dA + v) and c(r0, r0 + dA + 256 + v) in float64:
+  //      sum_t (x[r0+t] - mean_r0) * x[c + t]
+  float2 cov2[kVh];
   {
-    double acc[V];
+    double accA[kVh], accB[kVh], wa_[kVh], wbv[kVh];
+    const int baseA = r0 + dA, baseB = baseA + kHalf;
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.0;
-    const double mr = mu[r0];
-    for (int t = 0; t < m; ++t) {
-      const double av = static_cast<double>(x[r0 + t]) - mr;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int idx = r0 + dl + v + t;
-        double xv;
-        if (MASKED) xv = idx < n ? static_cast<double>(x[idx]) : 0.0;
-        else xv = static_cast<double>(x[idx]);
-        acc[v] = fma(av, xv, acc[v]);
-      }
+    for (int v = 0; v < kVh; ++v) {
+      accA[v] = 0.0;
+      accB[v] = 0.0;
+      wa_[v] = ld_guard(x, baseA + v, n);
+      wbv[v] = ld_guard(x, baseB + v, n);
     }
+    const double mr = a.wa.mu[wb + r0];
+    int t0 = 0;
+    for (; t0 + kVh <= m; t0 += kVh) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) cov[v] = static_cast<float>(acc[v]);
-  }
-
-  float cdf[V], cdg[V], cinv[V], ckey[V];
-  int cin[V];
+      for (int u = 0; u < kVh; ++u) {
+        const double at = static_cast<double>(x[r0 + t0 + u]) - mr;
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int j = r0 + dl + v;
-    cdf[v] = df[j];
-    cdg[v] = dg[j];
-    cinv[v] = inv[j];
-    ckey[v] = kEmpty;
-    cin[v] = -1;
-  }
-
-  const int nsteps = MASKED ? ((rEnd - r0 + V - 1) / V) * V : (rEnd - r0);
-  for (int s0 = 0; s0 < nsteps; s0 += V) {
-    const int ib = r0 + s0;
-    float rdf[V], rdg[V], rinv[V], ndf[V], ndg[V], ninv[V];
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      rdf[u] = df[ib + u];
-      rdg[u] = dg[ib + u];
-      rinv[u] = inv[ib + u];
-      const int j = ib + u + dl + V;
-      ndf[u] = df[j];
-      ndg[u] = dg[j];
-      ninv[u] = inv[j];
-    }
-#pragma unroll
-    for (int s = 0; s < V; ++s) {
-      const int i = ib + s;
-      float rowk = kEmpty;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int c = (v + s) % V;
-        const float rho = (cov[v] * cinv[c]) * rinv[s];
-        float key = tag_key(rho, static_cast<unsigned>(v));
-        if (MASKED) {
-          const int dd = dl + v;
-          const bool ok = (dd >= a.excl) && (i + dd < l) && (i < rEnd);
-          key = ok ? key : kEmpty;
+        for (int v = 0; v < kVh; ++v) {
+          accA[v] = fma(at, wa_[(v + u) & (kVh - 1)], accA[v]);
+          accB[v] = fma(at, wbv[(v + u) & (kVh - 1)], accB[v]);
         }
-        rowk = fmaxf(rowk, key);
-        ckey[c] = fmaxf(ckey[c], key);
-        cov[v] = fmaf(rdf[s], cdg[c], cov[v]);
-        cov[v] = fmaf(cdf[c], rdg[s], cov[v]);
-      }
-      const int slot = (s0 + s) & 31;
-      rowbuf[slot][lane] = rowk;
-      {
-        // the column in slot s % V (diagonal offset 0 of this lane) leaves the lane
-        const int c0 = s % V;
-        const float kl = ckey[c0];
-        const unsigned tag = __float_as_uint(kl) & 15u;
-        const int row = (tag == static_cast<unsigned>(kTagIn)) ? cin[c0] : (i - static_cast<int>(tag));
-        const float kin = __shfl_down_sync(TSK_FULL_MASK, kl, 1);
-        const int rin = __shfl_down_sync(TSK_FULL_MASK, row, 1);
-        if (lane == 0) { cbk[slot] = kl; cbr[slot] = row; }
-        ckey[c0] = (lane == 31) ? kEmpty : tag_key(kin, kTagIn);
-        cin[c0] = rin;
-        cdf[c0] = ndf[s];
-        cdg[c0] = ndg[s];
-        cinv[c0] = ninv[s];
+        wa_[u] = ld_guard(x, baseA + t0 + u + kVh, n);
+        wbv[u] = ld_guard(x, baseB + t0 + u + kVh, n);
       }
     }
-    if (((s0 + V) & 31) == 0) flush_rows_cols<V>(rowbuf, cbk, cbr, 32, r0 + s0 + V - 32, d0, l, best, lane);
-  }
-  const int rem = nsteps & 31;
-  if (rem) flush_rows_cols<V>(rowbuf, cbk, cbr, rem, r0 + nsteps - rem, d0, l, best, lane);
-  // columns still inside the band: slot v <-> column r0 + nsteps + dl + v
+    for (int t = t0; t < m; ++t) {
+      const double at = static_cast<double>(x[r0 + t]) - mr;
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int j = r0 + nsteps + dl + v;
-    const float kk = ckey[v];
-    if (kk > -2.f && j < l) {
-      const unsigned tag = __float_as_uint(kk) & 15u;
-      const int row = (tag == static_cast<unsigned>(kTagIn)) ? cin[v] : (j - dl - static_cast<int>(tag));
-      atomicMax(&best[j], tsk_pack(untag_key(kk), row));
+      for (int v = 0; v < kVh; ++v) {
+        accA[v] = fma(at, ld_guard(x, baseA + v + t, n), accA[v]);
+        accB[v] = fma(at, ld_guard(x, baseB + v + t, n), accB[v]);
+      }
     }
+#pragma unroll
+    for (int v = 0; v < kVh; ++v) cov2[v] = make_float2(static_cast<float>(accA[v]), static_cast<float>(accB[v]));
+  }
+
+  // ---- column state for the first row: slot v <-> columns r0 + dA + v (a) and + 256 (b)
+  float2 cdf2[kVh], cdg2[kVh], cinv2[kVh];
+  float ckA[kVh], ckB[kVh];
+  unsigned tagv[kVh];
+#pragma unroll
+  for (int v = 0; v < kVh; ++v) {
+    const int j = r0 + dA + v;
+    cdf2[v] = make_float2(df[j], df[j + kHalf]);
+    cdg2[v] = make_float2(dg[j], dg[j + kHalf]);
+    cinv2[v] = make_float2(inv[j], inv[j + kHalf]);
+    ckA[v] = kEmpty;
+    ckB[v] = kEmpty;
+    tagv[v] = static_cast<unsigned>(lane * kVh + v);
+  }
+
+  // ---- column ring: entry e <-> columns r0 + d0 + e (a) and + 256 (b)
+  const int colbase = r0 + d0;
+  auto ring_store = [&](int e, float vdf_a, float vdf_b, float vdg_a, float vdg_b, float vin_a, float vin_b) {
+    const int p = ring_phys(e % kRingEntries);
+    w.ring[0][p] = make_float2(vdf_a, vdf_b);
+    w.ring[1][p] = make_float2(vdg_a, vdg_b);
+    w.ring[2][p] = make_float2(vin_a, vin_b);
+  };
+  // initial fill: ring entries [8, 8 + kRingInit) and the rows of the first chunk
+  for (int e = kVh + lane; e < kVh + kRingInit; e += 32) {
+    const int j = colbase + e;
+    ring_store(e, df[j], df[j + kHalf], dg[j], dg[j + kHalf], inv[j], inv[j + kHalf]);
+  }
+  {
+    float2* rr = reinterpret_cast<float2*>(&w.rrow[0][0][0]);
+    const int i = r0 + lane;
+    rr[lane] = make_float2(df[i], df[i]);
+    rr[kChunk + lane] = make_float2(dg[i], dg[i]);
+    rr[2 * kChunk + lane] = make_float2(inv[i], inv[i]);
+  }
+
+  const int nsteps = MASKED ? ((rEnd - r0 + kChunk - 1) / kChunk) * kChunk : (rEnd - r0);
+  int ering = (kVh * (lane + 1)) % kRingEntries;  // ring slot of the column entering at step 0
+  for (int S0 = 0; S0 < nsteps; S0 += kChunk) {
+    const int buf = (S0 / kChunk) & 1;
+    // copies issued one chunk ago have landed; start those for the next chunk:
+    // ring entries kVh + kRingInit + S0 + lane and the rows of the next chunk
+    cp_async_wait_all();
+    __syncwarp();
+    {
+      const int e = kVh + kRingInit + S0 + lane;
+      const int j = colbase + e;
+      float* d0p = reinterpret_cast<float*>(&w.ring[0][ring_phys(e % kRingEntries)]);
+      float* d1p = reinterpret_cast<float*>(&w.ring[1][ring_phys(e % kRingEntries)]);
+      float* d2p = reinterpret_cast<float*>(&w.ring[2][ring_phys(e % kRingEntries)]);
+      cp_async4(d0p, df + j);
+      cp_async4(d0p + 1, df + j + kHalf);
+      cp_async4(d1p, dg + j);
+      cp_async4(d1p + 1, dg + j + kHalf);
+      cp_async4(d2p, inv + j);
+      cp_async4(d2p + 1, inv + j + kHalf);
+      float* rr = reinterpret_cast<float*>(&w.rrow[buf ^ 1][0][0]);
+      const int i = r0 + S0 + kChunk + lane;
+      cp_async4(rr + 2 * lane, df + i);
+      cp_async4(rr + 2 * lane + 1, df + i);
+      cp_async4(rr + 2 * kChunk + 2 * lane, dg + i);
+      cp_async4(rr + 2 * kChunk + 2 * lane + 1, dg + i);
+      cp_async4(rr + 4 * kChunk + 2 * lane, inv + i);
+      cp_async4(rr + 4 * kChunk + 2 * lane + 1, inv + i);
+      cp_async_commit();
+    }
+#pragma unroll 1
+    for (int sb = 0; sb < kChunk; sb += kVh) {  // 8-row blocks: one period of the slot rotation
+#pragma unroll
+    for (int gg = 0; gg < kVh / 2; ++gg) {
+      const int g = sb / 2 + gg;
+      const float4 rf4 = w.rrow[buf][0][g], rg4 = w.rrow[buf][1][g], ri4 = w.rrow[buf][2][g];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int sr = 2 * gg + h;   // step within the 8-row block (compile-time)
+        const int s = sb + sr;       // step within the chunk
+        const int i = r0 + S0 + s;
+        const float2 rdf2 = h ? make_float2(rf4.z, rf4.w) : make_float2(rf4.x, rf4.y);
+        const float2 rdg2 = h ? make_float2(rg4.z, rg4.w) : make_float2(rg4.x, rg4.y);
+        const float2 rinv2 = h ? make_float2(ri4.z, ri4.w) : make_float2(ri4.x, ri4.y);
+        float kA[kVh], kB[kVh];
+#pragma unroll
+        for (int v = 0; v < kVh; ++v) {
+          const int c = (v + sr) & (kVh - 1);
+          const float2 t = __fmul2_rn(cov2[v], cinv2[c]);
+          const float2 r = __fmul2_rn(t, rinv2);
+          float ka = tag_key(r.x, tagv[v]);
+          float kb = tag_key(r.y, tagv[v]);
+          if (MASKED) {
+            const bool rowok = i < rEnd;
+            ka = (rowok && i + dA + v < l) ? ka : kEmpty;
+            kb = (rowok && i + dA + kHalf + v < l) ? kb : kEmpty;
+          }
+          kA[v] = ka;
+          kB[v] = kb;
+          ckA[c] = fmaxf(ckA[c], ka);
+          ckB[c] = fmaxf(ckB[c], kb);
+          cov2[v] = __ffma2_rn(rdf2, cdg2[c], cov2[v]);
+          cov2[v] = __ffma2_rn(cdf2[c], rdg2, cov2[v]);
+        }
+        const float rka = fmaxf(max3f(max3f(max3f(kA[0], kA[1], kA[2]), kA[3], kA[4]), kA[5], kA[6]), kA[7]);
+        const float rkb = fmaxf(max3f(max3f(max3f(kB[0], kB[1], kB[2]), kB[3], kB[4]), kB[5], kB[6]), kB[7]);
+        w.rowbuf[s][lane ^ (s & 15)] = make_float2(rka, rkb);
+        // the columns in slot s % 8 (diagonal offset 0 of this lane) leave the lane
+        const int c0 = sr;
+        const float la = ckA[c0], lb = ckB[c0];
+        const float ia = __shfl_down_sync(TSK_FULL_MASK, la, 1);
+        const float ib = __shfl_down_sync(TSK_FULL_MASK, lb, 1);
+        if (lane == 0) w.colbuf[s] = make_float2(la, lb);
+        ckA[c0] = (lane == 31) ? kEmpty : ia;
+        ckB[c0] = (lane == 31) ? kEmpty : ib;
+        {
+          const int p = ring_phys(ering);
+          cdf2[c0] = w.ring[0][p];
+          cdg2[c0] = w.ring[1][p];
+          cinv2[c0] = w.ring[2][p];
+          ering = (ering + 1 == kRingEntries) ? 0 : ering + 1;
+        }
+      }
+    }
+    }
+    flush_chunk(w, kChunk, r0 + S0, d0, l, best, lane);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  // columns still inside the band: slot v <-> columns r0 + nsteps + dA + v (+ 256)
+#pragma unroll
+  for (int v = 0; v < kVh; ++v) {
+    const int j = r0 + nsteps + dA + v;
+    const int row0 = r0 + nsteps + lane * kVh + v;  // = j - d0
+    if (ckA[v] > -2.f && j < l)
+      atomicMax(&best[j], tsk_pack(untag_key(ckA[v]), row0 - static_cast<int>(__float_as_uint(ckA[v]) & 0xffu)));
+    if (ckB[v] > -2.f && j + kHalf < l)
+      atomicMax(&best[j + kHalf], tsk_pack(untag_key(ckB[v]), row0 - static_cast<int>(__float_as_uint(ckB[v]) & 0xffu)));
   }
 }
 
-template <int V, typename TX>
-__global__ void __launch_bounds__(kWarps * 32) k_mp_diag(MpArgs a) {
-  __shared__ float rowbuf[kWarps][32][33];
-  __shared__ float cbk[kWarps][32];
-  __shared__ int cbr[kWarps][32];
+template <typename TX>
+__global__ void __launch_bounds__(kWarps * 32, 3) k_mp_diag(MpArgs a) {
+  extern __shared__ __align__(16) unsigned char mp_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int D = 32 * V;
+  MpWarpSmem& w = reinterpret_cast<MpWarpSmem*>(mp_smem)[wid];
   for (;;) {
-    unsigned long long w = 0;
-    if (lane == 0) w = atomicAdd(a.counter, 1ull);
-    w = __shfl_sync(TSK_FULL_MASK, w, 0);
-    if (static_cast<int64_t>(w) >= a.total_tiles) break;
-    const int q = tsk_find_segment<int64_t>(a.tile_prefix, a.n_streams, static_cast<int64_t>(w));
-    const int t = static_cast<int>(static_cast<int64_t>(w) - a.tile_prefix[q]);
-    const int32_t* bp = a.band_prefix + a.band_off[q];
-    const int nb = static_cast<int>(a.band_off[q + 1] - a.band_off[q]) - 1;
-    const int b = tsk_find_segment<int32_t>(bp, nb, t);
-    const int r0 = (t - bp[b]) * a.H;
-    const int n = a.len[q];
-    const int l = n - a.m + 1;
-    const int d0 = a.excl4 + b * D;
-    const int dmin = max(d0, a.excl);
-    const int rEnd = min(r0 + a.H, l - dmin);
-    const TX* x = static_cast<const TX*>(a.X) + a.xoff[q];
-    const int64_t wb = a.woff[q];
-    const bool interior = (d0 >= a.excl) && (rEnd == r0 + a.H) && (rEnd - 1 + d0 + D - 1 <= l - 1);
-    if (interior)
-      mp_tile<V, false, TX>(a, x, n, l, wb, d0, r0, rEnd, rowbuf[wid], cbk[wid], cbr[wid], lane);
-    else
-      mp_tile<V, true, TX>(a, x, n, l, wb, d0, r0, rEnd, rowbuf[wid], cbk[wid], cbr[wid], lane);
+    // guided claim: a run of consecutive work units, long while much work
+    // remains (contiguous units of a band then share one float64 anchor),
+    // single units at the end (balance)
+    int w0 = 0, wend = 0;
+    if (lane == 0) {
+      const long long cur = static_cast<long long>(*reinterpret_cast<volatile unsigned long long*>(a.counter));
+      const long long remaining = a.total_tiles - cur;
+      const long long c = min(static_cast<long long>(kMaxClaim), max(1LL, remaining / (2LL * a.total_warps)));
+      const long long s0 = static_cast<long long>(atomicAdd(a.counter, static_cast<unsigned long long>(c)));
+      w0 = static_cast<int>(min(s0, static_cast<long long>(a.total_tiles)));
+      wend = static_cast<int>(min(s0 + c, static_cast<long long>(a.total_tiles)));
+    }
+    w0 = __shfl_sync(TSK_FULL_MASK, w0, 0);
+    wend = __shfl_sync(TSK_FULL_MASK, wend, 0);
+    if (w0 >= wend) break;
+    for (int wk = w0; wk < wend;) {
+      const int4 td = a.tiles[wk];
+      const int q = td.x, d0 = td.y, r0 = td.z;
+      int rEnd = td.w & 0x7fffffff;
+      const bool masked = td.w < 0;
+      ++wk;
+      if (!masked) {
+        // merge the following units that continue this band
+        while (wk < wend) {
+          const int4 nx = a.tiles[wk];
+          if (nx.w < 0 || nx.x != q || nx.y != d0 || nx.z != rEnd || nx.w - r0 > kMaxWalk) break;
+          rEnd = nx.w;
+          ++wk;
+        }
+      }
+      const int n = a.len[q];
+      const int l = n - a.m + 1;
+      const TX* x = static_cast<const TX*>(a.X) + a.xoff[q];
+      const int64_t wb = a.woff[q];
+      if (!masked)
+        mp_tile<false, TX>(a, x, n, l, wb, d0, r0, rEnd, w, lane);
+      else
+        mp_tile<true, TX>(a, x, n, l, wb, d0, r0, rEnd, w, lane);
+    }
   }
 }
 
@@ -546,15 +688,13 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
   a.len = plan.len;
   a.woff = plan.woff;
   a.tile_prefix = plan.tile_prefix;
-  a.band_off = plan.band_off;
-  a.band_prefix = plan.band_prefix;
+  a.tiles = plan.tiles;
   a.counter = counter;
   a.wa = wa;
   a.total_tiles = plan.total_tiles;
   a.n_streams = n_streams;
   a.m = m;
   a.excl = excl;
-  a.excl4 = excl & ~3;
   a.H = plan.H;
   if (plan.total_tiles > 0) {
     if (f64) {
@@ -564,14 +704,18 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
         TSK_LAUNCH_CHECK(ctx, "k_mp_diag_f64");
       }
     } else {
+      const size_t smem = sizeof(MpWarpSmem) * kWarps;
+      TSK_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mp_diag<TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem)));
       int per_sm = 0;
-      TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<kV, TX>, kWarps * 32, 0));
+      TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<TX>, kWarps * 32, smem));
       per_sm = std::max(per_sm, 1);
       const int64_t want = (plan.total_tiles + kWarps - 1) / kWarps;
       const int64_t grid = std::min<int64_t>(want, static_cast<int64_t>(per_sm) * ctx->sm_count);
+      a.total_warps = static_cast<int>(grid) * kWarps;
       {
         tsk_prof_scope ps(ctx, TSK_PROF_MP_DIAG);
-        k_mp_diag<kV, TX><<<static_cast<unsigned>(grid), kWarps * 32, 0, st>>>(a);
+        k_mp_diag<TX><<<static_cast<unsigned>(grid), kWarps * 32, smem, st>>>(a);
       }
       TSK_LAUNCH_CHECK(ctx, "k_mp_diag");
     }
@@ -590,7 +734,8 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
 
 }  // namespace
 
-int tsk_mp_band_width() { return kD; }
+int tsk_mp_band_width() { return kBand; }
+int tsk_mp_chunk_rows() { return kChunk; }
 int tsk_mp_pad() { return kPad; }
 int tsk_mp_chunk() { return kWinChunk; }
 

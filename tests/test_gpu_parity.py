@@ -46,7 +46,7 @@ def _streams(tsk, xs, m, excl, precision="fp32", rows=None, dtype=torch.float32)
 
 # --- matrix profile -----------------------------------------------------------
 
-@pytest.mark.parametrize("rows_per_unit", [2048, 64])
+@pytest.mark.parametrize("rows_per_unit", [0, 64, 32])
 def test_mp_selfjoin_fp32_ragged_streams(tsk, rows_per_unit):
     tsk.set_tile_rows(rows_per_unit)
     try:
@@ -60,7 +60,7 @@ def test_mp_selfjoin_fp32_ragged_streams(tsk, rows_per_unit):
             assert np.all(np.isnan(P[l:])) and np.all(I[l:] == -1)
             check_profile(x.astype(np.float64), m, excl, P[:l], I[:l])
     finally:
-        tsk.set_tile_rows(2048)
+        tsk.set_tile_rows(0)
 
 
 def test_mp_selfjoin_fp32_float64_input_and_odd_exclusion(tsk):
