@@ -218,6 +218,36 @@ TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, const int32_t*
                                const float* R, const float* S, int32_t n_series, const int32_t* series_len_host,
                                int32_t d, int32_t k, int32_t m, float* dT, float* dR);
 
+/*
+ * mp_selfjoin_static - the matrix profile of ONE float32 stream, like
+ * mp_selfjoin with precision TSK_MP_FP32, but without allocating any device
+ * memory and without a context.  The paper has no counterpart; this entry
+ * point exists for callers that cannot call cudaMalloc: code that runs after
+ * start-up in a real-time monitor that must not allocate, code whose device
+ * memory is owned by another framework's pool, or code called back from
+ * inside an allocator, where allocating again would deadlock or fail.
+ *
+ * All scratch (window statistics, the per-window maxima, the work list and
+ * counters) lives in one 3 MiB array in the library's global device memory;
+ * every GPU that loads the library holds that array until the process exits.
+ *   X      : device float32 [n] input stream (caller-owned).
+ *   P, I   : device float32 / int32 [n] outputs, as mp_selfjoin (entries
+ *            i >= l = n - m + 1 are NaN / -1).
+ *   cuda_stream : the cudaStream_t the work is issued on (NULL = default).
+ * Limits: 2 <= m <= 4096, m <= n, excl >= 1 and l <= 65536 windows; larger
+ * inputs are rejected with TSK_ERR_INVALID_ARG before anything is issued.
+ * The first call on a device looks up the array's device address and sets the
+ * kernels' shared-memory limits for that device (the device current at the
+ * call); make that first call before any CUDA-graph stream capture.  Every
+ * call uses the same array and leaves its contents behind (the call clears
+ * what must start at zero), so calls whose work may overlap on the GPU - on
+ * different streams, or from several host threads - race and must be
+ * serialised by the caller.  Non-finite input is not reported (no error word
+ * is read back); the outputs are then unspecified.
+ */
+TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int32_t m, int32_t excl, float* P, int32_t* I,
+                                      void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

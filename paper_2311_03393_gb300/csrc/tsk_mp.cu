@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 namespace {
 
@@ -753,4 +754,165 @@ tsk_status tsk_run_mp(tsk_ctx* ctx, const void* X, int x_dtype, int32_t n_stream
   if (x_dtype == TSK_F64)
     return run_typed<double>(ctx, static_cast<const double*>(X), n_streams, plan, m, excl, precision, P, I, ws);
   return run_typed<float>(ctx, static_cast<const float*>(X), n_streams, plan, m, excl, precision, P, I, ws);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant for one stream.
+//
+// All device scratch of the matrix-profile pipeline (window statistics, the
+// packed per-window maxima, the work list, counters) lives in one file-scope
+// __device__ array.  Host code never uses the array's name as an address: its
+// device address comes from cudaGetSymbolAddress, once per device.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(3) << 20;  // 3 MiB on every device that loads the library
+constexpr int kStaticMaxWindows = 65536;                   // l = n - m + 1 at most
+constexpr int kStaticMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+// Per-device set-up: the scratch array's device address and the kernels'
+// shared-memory limits.  Runs on the first call on each device.
+tsk_status static_setup(int dev, void** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return TSK_ERR_CUDA;
+    }
+    const int win_smem = static_cast<int>(sizeof(double) * 2 * (kWinChunk + 4096 + 2));
+    if (cudaFuncSetAttribute(k_window_stats<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, win_smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_mp_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sizeof(MpWarpSmem) * kWarps)) != cudaSuccess) {
+      cudaGetLastError();
+      return TSK_ERR_CUDA;
+    }
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return TSK_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int32_t m, int32_t excl, float* P,
+                                                 int32_t* I, void* cuda_stream) {
+  if (!X || !P || !I || m < 2 || m > 4096 || n < m || excl < 1) return TSK_ERR_INVALID_ARG;
+  const int64_t l = static_cast<int64_t>(n) - m + 1;
+  if (l > kStaticMaxWindows) return TSK_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return TSK_ERR_CUDA;
+  void* base = nullptr;
+  tsk_status st = static_setup(dev, &base);
+  if (st) return st;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TSK_ERR_CUDA;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+  // work list of the one stream: interior units of every band, then the band ends
+  const int64_t e = l - excl;
+  const double cells = e > 0 ? static_cast<double>(e) * (e + 1) / 2 : 0.0;
+  int32_t H = static_cast<int32_t>(std::min(8192.0, std::max(1024.0, cells / (sms * 12.0 * 64.0 * kBand))));
+  H = (H + kChunk - 1) / kChunk * kChunk;
+  std::vector<int4> tiles, tri;
+  for (int64_t d0 = excl; d0 < l; d0 += kBand) {
+    const int64_t rows = l - d0;
+    int64_t rint = std::max<int64_t>(0, rows - (kBand - 1));
+    rint -= rint % kChunk;
+    for (int64_t r0 = 0; r0 < rint; r0 += H)
+      tiles.push_back(make_int4(0, static_cast<int>(d0), static_cast<int>(r0), static_cast<int>(std::min<int64_t>(r0 + H, rint))));
+    if (rows > rint)
+      tri.push_back(make_int4(0, static_cast<int>(d0), static_cast<int>(rint),
+                              static_cast<int>(static_cast<uint32_t>(rows) | 0x80000000u)));
+  }
+  tiles.insert(tiles.end(), tri.begin(), tri.end());
+
+  // carve the scratch array
+  const int64_t W = (l + kPad + 3) & ~int64_t(3);
+  struct Head {
+    int64_t xoff[2], woff[2], chunk_prefix[2];
+    int32_t len[1];
+    uint8_t smask[4];
+  };
+  size_t off = 0;
+  const size_t o_head = off; off = align256(off + sizeof(Head));
+  const size_t o_mu = off; off = align256(off + 8 * W);
+  const size_t o_ss = off; off = align256(off + 8 * W);
+  const size_t o_inv = off; off = align256(off + 4 * W);
+  const size_t o_df = off; off = align256(off + 4 * W);
+  const size_t o_dg = off; off = align256(off + 4 * W);
+  const size_t o_best = off; off = align256(off + 8 * W);
+  const size_t o_nxt = off; off = align256(off + 4 * W);
+  const size_t o_small = off; off = align256(off + 64);  // constcnt, counter, error word
+  const size_t o_tiles = off; off = align256(off + sizeof(int4) * tiles.size());
+  if (off > kStaticScratchBytes) return TSK_ERR_INVALID_ARG;
+  char* sb = static_cast<char*>(base);
+  Head h{};
+  h.xoff[1] = n;
+  h.woff[1] = W;
+  h.chunk_prefix[1] = (l + kWinChunk - 1) / kWinChunk;
+  h.len[0] = n;
+  h.smask[0] = 1;
+  if (cudaMemcpyAsync(sb + o_head, &h, sizeof(Head), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      (!tiles.empty() && cudaMemcpyAsync(sb + o_tiles, tiles.data(), sizeof(int4) * tiles.size(),
+                                         cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
+      cudaMemsetAsync(sb + o_best, 0, 8 * W, stream) != cudaSuccess ||
+      cudaMemsetAsync(sb + o_small, 0, 64, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TSK_ERR_CUDA;
+  }
+  const Head* dh = reinterpret_cast<const Head*>(sb + o_head);
+  WinArrays wa{};
+  wa.mu = reinterpret_cast<double*>(sb + o_mu);
+  wa.ss = reinterpret_cast<double*>(sb + o_ss);
+  wa.inv = reinterpret_cast<float*>(sb + o_inv);
+  wa.df = reinterpret_cast<float*>(sb + o_df);
+  wa.dg = reinterpret_cast<float*>(sb + o_dg);
+  wa.best = reinterpret_cast<unsigned long long*>(sb + o_best);
+  wa.nxt = reinterpret_cast<int32_t*>(sb + o_nxt);
+  wa.constcnt = reinterpret_cast<int32_t*>(sb + o_small);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(sb + o_small + 8);
+  int* err = reinterpret_cast<int*>(sb + o_small + 16);
+
+  const size_t win_smem = sizeof(double) * 2 * (kWinChunk + m + 2);
+  k_window_stats<float><<<static_cast<unsigned>(h.chunk_prefix[1]), kWinThreads, win_smem, stream>>>(
+      X, dh->xoff, dh->len, dh->woff, dh->chunk_prefix, 1, m, 0, wa, err);
+  k_next_const<<<1, kWinThreads, 0, stream>>>(dh->len, dh->smask, dh->woff, m, wa);
+  if (!tiles.empty()) {
+    MpArgs a{};
+    a.X = X;
+    a.xoff = dh->xoff;
+    a.len = dh->len;
+    a.woff = dh->woff;
+    a.tiles = reinterpret_cast<const int4*>(sb + o_tiles);
+    a.counter = counter;
+    a.wa = wa;
+    a.total_tiles = static_cast<int64_t>(tiles.size());
+    a.n_streams = 1;
+    a.m = m;
+    a.excl = excl;
+    a.H = H;
+    const size_t smem = sizeof(MpWarpSmem) * kWarps;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<float>, kWarps * 32, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return TSK_ERR_CUDA;
+    }
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>((a.total_tiles + kWarps - 1) / kWarps, static_cast<int64_t>(per_sm) * sms);
+    a.total_warps = static_cast<int>(grid) * kWarps;
+    k_mp_diag<float><<<static_cast<unsigned>(grid), kWarps * 32, smem, stream>>>(a);
+  }
+  k_mp_refine<float, float><<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
+      X, dh->xoff, dh->len, dh->smask, dh->woff, 1, n, m, excl, 0, wa, P, I);
+  if (cudaGetLastError() != cudaSuccess) return TSK_ERR_CUDA;
+  return TSK_OK;
 }
