@@ -73,8 +73,9 @@ enum {
 
 /* arithmetic of the matrix profile */
 enum {
-  TSK_MP_FP32 = 0, /* float32 diagonal recurrence with float64 anchors and a float64
-                      re-evaluation of every row's chosen neighbour; P is float32  */
+  TSK_MP_FP32 = 0, /* float32 diagonal recurrence with float64 anchors, then an exact
+                      re-evaluation of every row's chosen neighbour (compensated
+                      float32 sums for float32 input); P is float32             */
   TSK_MP_FP64 = 1  /* float64 throughout; P is float64                            */
 };
 
@@ -99,7 +100,7 @@ TSK_API tsk_status tsk_mp_workspace_bytes(tsk_ctx* ctx, int32_t n_streams, const
  * passed (the work keeps running; call again). */
 TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s);
 /* Rows per matrix-profile work unit (a band of 512 diagonals x `rows` rows):
- * 0 = automatic (about 64 units per resident warp, 1024..8192), else a
+ * 0 = automatic (about 64 units per resident warp, 2048..8192), else a
  * multiple of 32 in [32, 1 << 20].  Smaller units balance short streams,
  * larger ones amortise the float64 anchors. */
 TSK_API tsk_status tsk_set_tile_rows(tsk_ctx* ctx, int32_t rows);

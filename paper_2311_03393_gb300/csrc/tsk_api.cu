@@ -166,7 +166,7 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
   const int32_t D = tsk_mp_band_width();
   int32_t H = ctx->mp_H;
   if (H <= 0) {
-    // rows per work unit: about 64 units per resident warp, within [1024, 8192]
+    // rows per work unit: about 64 units per resident warp, within [2048, 8192]
     // (warps claim runs of consecutive units, so small units cost few anchors)
     double cells = 0.0;
     for (int q = 0; q < n; ++q) {
@@ -177,7 +177,7 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
     const double warps = static_cast<double>(ctx->sm_count) * 12.0;
     const double rows = cells / (warps * 64.0 * D);
     const int32_t step = tsk_mp_chunk_rows();
-    H = static_cast<int32_t>(std::min(8192.0, std::max(1024.0, rows)));
+    H = static_cast<int32_t>(std::min(8192.0, std::max(2048.0, rows)));
     H = (H + step - 1) / step * step;
   }
   std::string key = "mp";

@@ -21,9 +21,9 @@
 //                       offset in their 4 low mantissa bits, so a max also knows
 //                       its argmax.  Results merge into a packed (key, index)
 //                       64-bit word per window with atomicMax.
-//   4. k_mp_refine      for every window: its chosen neighbour's distance in
-//                       float64, dist = sqrt(2 m (1 - rho)), plus the constant-
-//                       window rules.
+//   4. k_mp_refine      for every window: its chosen neighbour's distance,
+//                       dist = sqrt(2 m (1 - rho)) with rho re-evaluated exactly
+//                       (compensated sums), plus the constant-window rules.
 // The float64 variant (k_mp_diag_f64) is exact: one thread per diagonal, a
 // first pass takes the float64 maximum per window, a second pass the lowest
 // index attaining it.
@@ -417,6 +417,13 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
     }
 #pragma unroll 1
     for (int sb = 0; sb < kChunk; sb += kVh) {  // 8-row blocks: one period of the slot rotation
+    // in a block the entering columns use ring slots ering .. ering + 7 (ering is a
+    // multiple of 8, so the swizzle is a fixed XOR: slot ering + (sr ^ rx))
+    const float2* ringb = &w.ring[0][ering];
+    const int rx = (ering >> 4) & 7;
+    ering = (ering + kVh == kRingEntries) ? 0 : ering + kVh;
+    float2* rowp = &w.rowbuf[sb][0];
+    const int lx = lane ^ (sb & 8);  // row-buffer swizzle: lane ^ (step & 15) = lx ^ sr
 #pragma unroll
     for (int gg = 0; gg < kVh / 2; ++gg) {
       const int g = sb / 2 + gg;
@@ -451,7 +458,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
         }
         const float rka = fmaxf(max3f(max3f(max3f(kA[0], kA[1], kA[2]), kA[3], kA[4]), kA[5], kA[6]), kA[7]);
         const float rkb = fmaxf(max3f(max3f(max3f(kB[0], kB[1], kB[2]), kB[3], kB[4]), kB[5], kB[6]), kB[7]);
-        w.rowbuf[s][lane ^ (s & 15)] = make_float2(rka, rkb);
+        rowp[sr * 32 + (lx ^ sr)] = make_float2(rka, rkb);
         // the columns in slot s % 8 (diagonal offset 0 of this lane) leave the lane
         const int c0 = sr;
         const float la = ckA[c0], lb = ckB[c0];
@@ -461,11 +468,10 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
         ckA[c0] = (lane == 31) ? kEmpty : ia;
         ckB[c0] = (lane == 31) ? kEmpty : ib;
         {
-          const int p = ring_phys(ering);
-          cdf2[c0] = w.ring[0][p];
-          cdg2[c0] = w.ring[1][p];
-          cinv2[c0] = w.ring[2][p];
-          ering = (ering + 1 == kRingEntries) ? 0 : ering + 1;
+          const int o = sr ^ rx;
+          cdf2[c0] = ringb[o];
+          cdg2[c0] = ringb[kRingEntries + o];
+          cinv2[c0] = ringb[2 * kRingEntries + o];
         }
       }
     }
@@ -584,8 +590,54 @@ __global__ void __launch_bounds__(128) k_mp_diag_f64(MpArgs a, int pass) {
 }
 
 // ---------------------------------------------------------------------------
-// 4. refinement: float64 distance to each window's chosen neighbour
+// 4. refinement: exact distance to each window's chosen neighbour
 // ---------------------------------------------------------------------------
+// Correlation of windows i and j of a float32 series, accurate to ~1e-12.
+// Both windows are centred in float32 with a two-term mean (the centred values
+// carry a rounding of at most ~2^-24 of themselves, an input-sized
+// perturbation), then sum(ab), sum(aa), sum(bb) are accumulated with
+// error-free float32 transforms: each product is p + e with p = fl(ab),
+// e = fma(a, b, -p), and each running sum is a (hi, lo) pair updated by a
+// two-sum.  All three sums see the same values, so equal windows give rho = 1.
+struct DSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, pe));
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
+__device__ __forceinline__ double window_rho(const float* __restrict__ x, int i, int j, int m, double mi, double mj) {
+  const float mih = static_cast<float>(mi), mil = static_cast<float>(mi - static_cast<double>(mih));
+  const float mjh = static_cast<float>(mj), mjl = static_cast<float>(mj - static_cast<double>(mjh));
+  DSum sab, saa, sbb;
+  for (int t = 0; t < m; ++t) {
+    const float a = __fsub_rn(__fsub_rn(x[i + t], mih), mil);
+    const float b = __fsub_rn(__fsub_rn(x[j + t], mjh), mjl);
+    sab.add_prod(a, b);
+    saa.add_prod(a, a);
+    sbb.add_prod(b, b);
+  }
+  return sab.value() / sqrt(saa.value() * sbb.value());
+}
+// float64 series: the same correlation with float64 sums
+__device__ __forceinline__ double window_rho(const double* __restrict__ x, int i, int j, int m, double mi, double mj) {
+  double sab = 0.0, saa = 0.0, sbb = 0.0;
+  for (int t = 0; t < m; ++t) {
+    const double a = x[i + t] - mi, b = x[j + t] - mj;
+    sab = fma(a, b, sab);
+    saa = fma(a, a, saa);
+    sbb = fma(b, b, sbb);
+  }
+  return sab / sqrt(saa * sbb);
+}
+
 template <typename TX, typename TP>
 __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, const int64_t* __restrict__ xoff,
                                                    const int32_t* __restrict__ len, const uint8_t* __restrict__ smask,
@@ -637,10 +689,7 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
     if (wa.inv[wb + j] == 0.f) {
       dist = sqm;
     } else {
-      const double mi = wa.mu[wb + i];
-      double c = 0.0;
-      for (int t = 0; t < m; ++t) c = fma(static_cast<double>(x[i + t]) - mi, static_cast<double>(x[j + t]), c);
-      const double rho = c / (sqrt(wa.ss[wb + i]) * sqrt(wa.ss[wb + j]));
+      const double rho = window_rho(x, i, j, m, wa.mu[wb + i], wa.mu[wb + j]);
       dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - rho)));
     }
   }
@@ -820,7 +869,7 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   // work list of the one stream: interior units of every band, then the band ends
   const int64_t e = l - excl;
   const double cells = e > 0 ? static_cast<double>(e) * (e + 1) / 2 : 0.0;
-  int32_t H = static_cast<int32_t>(std::min(8192.0, std::max(1024.0, cells / (sms * 12.0 * 64.0 * kBand))));
+  int32_t H = static_cast<int32_t>(std::min(8192.0, std::max(2048.0, cells / (sms * 12.0 * 64.0 * kBand))));
   H = (H + kChunk - 1) / kChunk * kChunk;
   std::vector<int4> tiles, tri;
   for (int64_t d0 = excl; d0 < l; d0 += kBand) {
