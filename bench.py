@@ -38,9 +38,9 @@ UNIT = "cell-updates/s"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
-# Per-cell DRAM traffic of k_mp_diag from an ncu capture (None until taken for
-# the current kernel); see profiles/mp_diag_ncu.md.
-MP_DIAG_DRAM_BYTES_PER_CELL = None
+# DRAM bytes (read + write) of the k_mp_diag launches of one step, from one ncu
+# capture per workload (profiles/launches_water_bench.md); None where not taken.
+MP_DIAG_DRAM_BYTES = {"water": [10280960, 10442496, 64885248]}
 
 WORKLOADS = {
     # name: (synth workload index, top-K, description)
@@ -332,8 +332,8 @@ def run_gpu(args):
     cells_in_mp = cps * (k + n_dirty + d) * args.steps
     achieved = 4.0 * cells_in_mp / (mp_ms / 1000.0) / 1e12 if mp_ms > 0 else None
     traffic = None
-    if MP_DIAG_DRAM_BYTES_PER_CELL is not None and mp_launches:
-        traffic = MP_DIAG_DRAM_BYTES_PER_CELL * cells_in_mp / mp_launches
+    if args.workload in MP_DIAG_DRAM_BYTES:
+        traffic = float(np.mean(MP_DIAG_DRAM_BYTES[args.workload]))
     clocks = clk.summary()
     sketch_bytes = (2 * 4 * d * n + 4 * k * n)  # stats pass + sketch pass over T, write S
     sketch_flops = 2.0 * d * k * n
