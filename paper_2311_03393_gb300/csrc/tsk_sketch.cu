@@ -57,6 +57,48 @@ __global__ void __launch_bounds__(kStatThreads) k_colstats(const TIn* __restrict
 // Normalised element in float64: (x - mu) / sigma, 0 for a constant stream.
 __device__ __forceinline__ double tsk_tbar(double x, double mu, double rinv) { return (x - mu) * rinv; }
 
+// Per-stream constants of the float32 fast path: mu = muh + mul, 1/sigma ~ rh,
+// and the absolute part of the error bound.
+struct NormC {
+  double mu, r;   // float64 mean and 1/sigma (the reference)
+  float muh, mul, rh, babs;
+};
+__device__ __forceinline__ NormC make_normc(double mu, double r) {
+  NormC c;
+  c.mu = mu;
+  c.r = r;
+  c.muh = static_cast<float>(mu);
+  c.mul = static_cast<float>(mu - static_cast<double>(c.muh));
+  c.rh = static_cast<float>(r);
+  c.babs = static_cast<float>(0x1p-45 * r * fabs(mu));
+  return c;
+}
+
+// bfloat16 of the float64 value (x - mu) * r, computed without float64 in almost
+// all cases.  v = ((x - muh) - mul) * rh in float32 differs from the float64
+// value by at most 2^-21 |v| + 2^-45 r (|mu| + |x|) (four float32 roundings
+// plus the two-term mean's residual); when v is farther than that from every
+// bfloat16 rounding midpoint its round-to-nearest-even is the float64 value's,
+// otherwise (about 1e-4 of elements) the float64 value is formed and rounded.
+__device__ __forceinline__ uint16_t tbar_bf16(float x, const NormC& c) {
+  const float v = __fmul_rn(__fsub_rn(__fsub_rn(x, c.muh), c.mul), c.rh);
+  const uint32_t bits = __float_as_uint(v);
+  const int ex = static_cast<int>((bits >> 23) & 0xffu);
+  if (ex >= 40 && ex < 255) {
+    const float ulp = __uint_as_float(static_cast<uint32_t>(ex - 23) << 23);
+    const int dist = abs(static_cast<int>(bits & 0xffffu) - 0x8000);
+    const float bound = __fmaf_rn(0x1p-21f, fabsf(v), c.babs + 0x1p-45f * c.rh * fabsf(x));
+    if (static_cast<float>(dist - 1) * ulp > bound) {
+      const uint32_t rnd = 0x7fffu + ((bits >> 16) & 1u);
+      return static_cast<uint16_t>((bits + rnd) >> 16);
+    }
+  }
+  return tsk_f64_to_bf16_bits(tsk_tbar(static_cast<double>(x), c.mu, c.r));
+}
+__device__ __forceinline__ uint16_t tbar_bf16(double x, const NormC& c) {
+  return tsk_f64_to_bf16_bits(tsk_tbar(x, c.mu, c.r));
+}
+
 // ---------------------------------------------------------------------------
 // bfloat16 tensor-core sketch.  One CTA = 64 time points of one series x all
 // k outputs; 4 warps, one m16 tile each, ceil(k/8) n8 tiles; K = d in chunks
@@ -74,7 +116,7 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restric
                                                            const double* __restrict__ stats, float* __restrict__ S) {
   __shared__ __align__(16) uint16_t As[kSkT][kSkPad];
   __shared__ __align__(16) uint16_t Bs[64][kSkPad];
-  __shared__ double smu[16], srinv[16];
+  __shared__ NormC snc[16];
 
   const int s = tsk_find_segment<int64_t>(blk_prefix, n_series, static_cast<int64_t>(blockIdx.x));
   const int n = len[s];
@@ -98,8 +140,7 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restric
         const double sg = stats[2 * (static_cast<int64_t>(s) * d + j) + 1];
         ri = sg > 0.0 ? 1.0 / sg : 0.0;
       }
-      smu[tid] = mu;
-      srinv[tid] = ri;
+      snc[tid] = make_normc(mu, ri);
     }
     __syncthreads();
 #pragma unroll
@@ -108,7 +149,7 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restric
       const int jl = e / kSkT, tl = e % kSkT;
       const int j = j0 + jl, t = t0 + tl;
       uint16_t h = 0;
-      if (j < d && t < n) h = tsk_f64_to_bf16_bits(tsk_tbar(tsk_ld(T, tbase + static_cast<int64_t>(j) * n + t), smu[jl], srinv[jl]));
+      if (j < d && t < n) h = tbar_bf16(T[tbase + static_cast<int64_t>(j) * n + t], snc[jl]);
       As[tl][jl] = h;
     }
     for (int e = tid; e < 16 * NT * 8; e += kSkThreads) {
@@ -211,7 +252,7 @@ __global__ void k_update_dims(Acc* __restrict__ S, const TIn* __restrict__ Td, c
     const double tb = tsk_tbar(tsk_ld(Td, dbase + static_cast<int64_t>(q) * n + t), mu, ri);
     const Acc sign = static_cast<Acc>(op[q]);
     if (precision == TSK_SKETCH_BF16) {
-      const float x = tsk_bf16_bits_to_f32(tsk_f64_to_bf16_bits(tb));
+      const float x = tsk_bf16_bits_to_f32(tbar_bf16(Td[dbase + static_cast<int64_t>(q) * n + t], make_normc(mu, ri)));
       for (int g = 0; g < k; ++g) {
         const float r = tsk_bf16_bits_to_f32(tsk_f64_to_bf16_bits(static_cast<double>(Rrows[q * k + g])));
         if (r != 0.f) S[sbase + static_cast<int64_t>(g) * n + t] += sign * static_cast<Acc>(r * x);
