@@ -48,6 +48,7 @@ WORKLOADS = {
     "traffic": (3, 10, "traffic-like sensors d=1024 n=100000 m=144 k=16 (10 planted discords)"),
     "grad": (5, 3, "random walks d=64 n=20000 m=100 k=8 (3 planted discords)"),
     "rw_small": (1, 3, "random walks d=8 n=2000 m=100 k=4 (1 planted discord)"),
+    "batched": (4, 1, "4096 random-walk series d=16 n~U{1000..32000} m=64 k=4 (1 planted discord each)"),
 }
 
 
@@ -61,6 +62,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the timed oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--graph", action="store_true", help="capture the step in a CUDA graph and replay it")
     return p.parse_args()
 
 
@@ -150,7 +152,7 @@ def oracle_sample(wl, seconds: float, rng_seed: int = 0):
     one oracle row evaluates every admissible j, i.e. two half-pairs per cell.
     """
     from oracle import tsk_oracle as o
-    T = wl.series[0]
+    T = max(wl.series, key=lambda a: a.shape[1])
     m = wl.m
     excl = int(math.ceil(m / 4))
     t0 = time.perf_counter()
@@ -219,31 +221,44 @@ def run_gpu(args):
         torch.cuda.set_device(0)
     build.build()
     import paper_2311_03393_gb300 as tsk
+    from paper_2311_03393_gb300 import autotune
 
     wl, K, desc = build_workload(args.workload, rank)
-    T_np = wl.series[0]
-    d, n = T_np.shape
+    d = wl.d
     m, k = wl.m, wl.k
+    lens = wl.lengths
+    ns = len(lens)
     excl = int(math.ceil(m / 4))
-    lens = [n]
     dev = torch.device("cuda", torch.cuda.current_device())
-    T_host = torch.from_numpy(np.ascontiguousarray(T_np.astype(np.float32).ravel())).pin_memory()
+    T_np = np.concatenate([s.astype(np.float32).ravel() for s in wl.series])
+    T_host = torch.from_numpy(T_np).pin_memory()
     T = T_host.to(dev)
     R = torch.from_numpy(wl.R).to(dev)
     del_dim = d // 2
     R_del = wl.R[del_dim:del_dim + 1]
-    slen_k = [n] * k
-    slen_d = [n] * d
-    S = torch.empty(k * n, dtype=torch.float32, device=dev)
-    stats = torch.empty((1, d, 2), dtype=torch.float64, device=dev)
-    bufs = {name: (torch.empty(cnt * n, dtype=torch.float32, device=dev),
-                   torch.empty(cnt * n, dtype=torch.int32, device=dev))
+    # the deleted dimension of every series, packed (a copy made once, outside the timed region)
+    off = np.concatenate([[0], np.cumsum([d * n for n in lens])])
+    T_del = torch.cat([T[int(off[s]) + del_dim * n: int(off[s]) + (del_dim + 1) * n] for s, n in enumerate(lens)])
+    total = int(sum(lens))
+    slen_k = [n for n in lens for _ in range(k)]
+    slen_d = [n for n in lens for _ in range(d)]
+    S = torch.empty(k * total, dtype=torch.float32, device=dev)
+    stats = torch.empty((ns, d, 2), dtype=torch.float64, device=dev)
+    bufs = {name: (torch.empty(cnt * total, dtype=torch.float32, device=dev),
+                   torch.empty(cnt * total, dtype=torch.int32, device=dev))
             for name, cnt in (("s", k), ("u", k), ("e", d))}
-    dscore = torch.ones((1, K), dtype=torch.float32, device=dev)
+    dscore = torch.ones((ns, K), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
 
-    def step(Tin, ev=None):
+    # rows per work unit of the matrix-profile kernel, tuned per layout (cached)
+    tsk.ts_sketch_build(T, R, lens, d, precision="bf16", out=S, stats=stats)
+    for X, sl in ((S, slen_k), (T, slen_d)):
+        if autotune.rows_for(sl, m, excl) == 0:
+            autotune.tune(X, sl, m, excl, reps=1)
+
+    def step(Tin, ev=None, Tdel=T_del):
+        stream = torch.cuda.current_stream()
+
         def mark(i):
             if ev is not None:
                 ev[i].record(stream)
@@ -255,8 +270,9 @@ def run_gpu(args):
         idx, grp, score, nn = top_s
         tsk.mp_backward(dscore, idx, grp, nn, Tin, stats, R, S, lens, d, m)
         mark(2)
-        dirty, _ = tsk.ts_sketch_update_dims(S, Tin[del_dim * n:(del_dim + 1) * n], lens, R_del, [-1])
-        Pu, Iu = tsk.mp_selfjoin(S, slen_k, m, excl, mask=dirty, P=bufs["u"][0], I=bufs["u"][1])
+        dirty, _ = tsk.ts_sketch_update_dims(S, Tdel, lens, R_del, [-1])
+        mask = np.tile(dirty, ns)
+        Pu, Iu = tsk.mp_selfjoin(S, slen_k, m, excl, mask=mask, P=bufs["u"][0], I=bufs["u"][1])
         top_u = tsk.discord_topk(Pu, Iu, lens, k, m, K)
         mark(3)
         Pe, Ie = tsk.mp_selfjoin(Tin, slen_d, m, excl, P=bufs["e"][0], I=bufs["e"][1])
@@ -264,13 +280,24 @@ def run_gpu(args):
         mark(4)
         return top_s, top_u, top_e, dirty
 
-    cps = cells_per_stream(n, m, excl)
+    cps = sum(cells_per_stream(n, m, excl) for n in lens)
+    l0 = tsk.launch_count()
     for _ in range(args.warmup):
         _, _, _, dirty = step(T)
     torch.cuda.synchronize()
+    launches_per_step = (tsk.launch_count() - l0) // max(1, args.warmup)
     n_dirty = int(np.sum(dirty))
     cells_step = cps * (k + n_dirty + d)
     cells_sketched = cps * k
+
+    graph = None
+    if args.graph:
+        # the whole step captured once, replayed per timed step
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step(T)
+        graph.replay()
+        torch.cuda.synchronize()
 
     # --- device-timed steps (inputs resident in HBM, L2 flushed before each step)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -284,9 +311,18 @@ def run_gpu(args):
     with ClockSampler(torch.cuda.current_device()) as clk:
         for s in range(args.steps):
             flush.fill_(float(s))
-            step(T, ev[s])
+            if graph is None:
+                step(T, ev[s])
+            else:
+                stream = torch.cuda.current_stream()
+                ev[s][0].record(stream)
+                graph.replay()
+                for i in range(1, 5):
+                    ev[s][i].record(stream)
         torch.cuda.synchronize()
     launches = tsk.launch_count() - launches0
+    if graph is not None:
+        launches = launches_per_step * args.steps  # the replayed graph holds one step's launches
     tsk.profile_enable(False)
     mp_ms, mp_launches = tsk.profile_read("mp_diag")
     sk_ms, sk_launches = tsk.profile_read("sketch")
@@ -299,13 +335,24 @@ def run_gpu(args):
     # --- end to end through the public API: pinned host T in, discords out
     e2e = None
     if not args.no_e2e:
-        out_host = torch.empty(3 * 4 * K, dtype=torch.float32).pin_memory()
+        out_host = torch.empty(3 * 4 * K * ns, dtype=torch.float32).pin_memory()
         h2d = T_host.numel() * 4
         d2h = out_host.numel() * 4
         Tdev = torch.empty_like(T)
-        for _ in range(2):
+        Tdel_dev = torch.empty_like(T_del)
+        stream = torch.cuda.current_stream()
+
+        def e2e_step():
             Tdev.copy_(T_host, non_blocking=True)
-            step(Tdev)
+            Tdel_dev.copy_(torch.cat([Tdev[int(off[s]) + del_dim * n: int(off[s]) + (del_dim + 1) * n]
+                                      for s, n in enumerate(lens)]))
+            top_s, top_u, top_e, _ = step(Tdev, Tdel=Tdel_dev)
+            res = torch.cat([torch.stack([t[1].float().ravel(), t[0].float().ravel(), t[2].float().ravel(),
+                                          t[3].float().ravel()]).ravel() for t in (top_s, top_u, top_e)])
+            out_host.copy_(res, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
         torch.cuda.synchronize()
         e_ms = []
         for s in range(args.steps):
@@ -313,11 +360,7 @@ def run_gpu(args):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            Tdev.copy_(T_host, non_blocking=True)
-            top_s, top_u, top_e, _ = step(Tdev)
-            res = torch.cat([torch.stack([t[1].float().ravel(), t[0].float().ravel(), t[2].float().ravel(),
-                                          t[3].float().ravel()]).ravel() for t in (top_s, top_u, top_e)])
-            out_host.copy_(res, non_blocking=True)
+            e2e_step()
             b.record(stream)
             b.synchronize()
             e_ms.append(a.elapsed_time(b))
@@ -335,14 +378,13 @@ def run_gpu(args):
     if args.workload in MP_DIAG_DRAM_BYTES:
         traffic = float(np.mean(MP_DIAG_DRAM_BYTES[args.workload]))
     clocks = clk.summary()
-    sketch_bytes = (2 * 4 * d * n + 4 * k * n)  # stats pass + sketch pass over T, write S
-    sketch_flops = 2.0 * d * k * n
+    sketch_flops = 2.0 * d * k * total
     sketch_info = None
     if sk_ms > 0:
         per = sk_ms / sk_launches / 1000.0
+        by = 4 * d * total + 4 * k * total
         sketch_info = {"kernel": "k_sketch_bf16", "ms_per_launch": per * 1000.0,
-                       "hbm_gbs": (4 * d * n + 4 * k * n) / per / 1e9,
-                       "hbm_frac": (4 * d * n + 4 * k * n) / per / 1e9 / peaks["hbm_gbs"],
+                       "hbm_gbs": by / per / 1e9, "hbm_frac": by / per / 1e9 / peaks["hbm_gbs"],
                        "bf16_tflops": sketch_flops / per / 1e12,
                        "bf16_frac": sketch_flops / per / 1e12 / peaks["bf16_tflops"]}
     parts = part.mean(axis=0)
@@ -350,13 +392,14 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "parallelism": f"replicas{ws}", "sketch": "bf16 tensor cores, f32 accumulate",
-                   "mp": "f32 diagonal recurrence, f64 anchors and refinement", "l2": "flushed before each step",
-                   "cells_per_step": cells_step, "top_k": K},
-        "parts_ms": {"sketched_mining": parts[0], "adjoint": parts[1], "dim_update_and_reprofile": parts[2],
-                     "exact_mining": parts[3]},
-        "speedup_exact_over_sketched": parts[3] / parts[0] if parts[0] > 0 else None,
-        "sketched_mining_cells_per_s": cells_sketched / (parts[0] / 1000.0),
+        "config": {"workload": desc, "series": ns, "parallelism": f"replicas{ws}",
+                   "sketch": "bf16 tensor cores, f32 accumulate",
+                   "mp": "f32 diagonal recurrence, f64 anchors, exact refinement", "l2": "flushed before each step",
+                   "cells_per_step": cells_step, "top_k": K, "cuda_graph": graph is not None,
+                   "tile_rows": {"sketch": autotune.rows_for(slen_k, m, excl),
+                                 "exact": autotune.rows_for(slen_d, m, excl)}},
+        "speedup_exact_over_sketched": None,
+        "sketched_mining_cells_per_s": None,
         "roofline": {"bound": "alu", "kernel": "k_mp_diag", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s", "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
                      "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {clock_mhz:.0f} MHz "
@@ -367,6 +410,11 @@ def run_gpu(args):
         "gpu_launches": launches,
         "e2e": e2e,
     }
+    if graph is None:
+        line["parts_ms"] = {"sketched_mining": parts[0], "adjoint": parts[1], "dim_update_and_reprofile": parts[2],
+                            "exact_mining": parts[3]}
+        line["speedup_exact_over_sketched"] = parts[3] / parts[0] if parts[0] > 0 else None
+        line["sketched_mining_cells_per_s"] = cells_sketched / (parts[0] / 1000.0)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         c, el, rows, sdesc = oracle_sample(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": c / el, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc}

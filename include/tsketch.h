@@ -143,7 +143,9 @@ TSK_API tsk_status ts_sketch_build(tsk_ctx* ctx, const void* T, int32_t t_dtype,
  *   S[s][g][t] += op[q] * R_rows[q][g] * T_bar_dims[s][q][t],  op = +1 add, -1 delete.
  * Deleting a dimension with the same raw stream and R row it was built with
  * restores the sketch without it (up to float32 rounding of S).
- *   R_rows_host : float32 nd x k, HOST memory.
+ *   R_rows_host : float32 nd x k, HOST memory (copied to the device once per
+ *                 distinct content and cached, so a repeated update can be
+ *                 captured in a CUDA graph).
  *   op_host     : int8 [nd], each +1 or -1, HOST memory.
  *   S           : sketch from ts_sketch_build (same k, precision), updated in place.
  *   stats       : output float64 [n_series][nd][2] for the listed dims; may be NULL.

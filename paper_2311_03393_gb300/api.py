@@ -120,10 +120,16 @@ def ts_sketch_update_dims(S: torch.Tensor, T_dims: torch.Tensor, series_len: Seq
 
 def mp_selfjoin(X: torch.Tensor, stream_len: Sequence[int], m: int, excl: int | None = None,
                 precision: str = "fp32", mask=None, P: torch.Tensor | None = None,
-                I: torch.Tensor | None = None):
-    """Self-join matrix profile of every stream (Def. 6).  Returns (P, I) packed like X."""
+                I: torch.Tensor | None = None, tile_rows: int | None = None):
+    """Self-join matrix profile of every stream (Def. 6).  Returns (P, I) packed like X.
+
+    tile_rows: rows per work unit of the diagonal kernel; None uses the
+    autotuner's cached choice for this layout (0, automatic, when untuned).
+    """
     _need_cuda(X)
     excl = default_excl(m) if excl is None else int(excl)
+    from . import autotune
+    rows = autotune.rows_for(stream_len, m, excl) if tile_rows is None else int(tile_rows)
     pdt = torch.float64 if precision == "fp64" else torch.float32
     if P is None:
         P = torch.empty(X.numel(), dtype=pdt, device=X.device)
@@ -136,6 +142,7 @@ def mp_selfjoin(X: torch.Tensor, stream_len: Sequence[int], m: int, excl: int | 
         mk = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
         mp = mk.ctypes.data_as(C.c_void_p)
     h = _ctx(X.device)
+    N.check(N.lib().tsk_set_tile_rows(h, rows), h, "tsk_set_tile_rows")
     N.check(N.lib().mp_selfjoin(h, _ptr(X), _dtype_code(X), len(stream_len), lp, mp, int(m), excl,
                                 MP_PRECISION[precision], _ptr(P), _ptr(I)), h, "mp_selfjoin")
     return P, I

@@ -519,15 +519,24 @@ extern "C" TSK_API tsk_status ts_sketch_update_dims(tsk_ctx* ctx, void* S, const
   BatchLayout L{};
   if ((st = batch_layout(ctx, n_series, series_len_host, nd, &L))) return st;
   const size_t nstat = static_cast<size_t>(n_series) * nd * 2;
-  const size_t need = tsk_carver::bytes_for(nstat, 8) + tsk_carver::bytes_for(static_cast<size_t>(nd) * k, 4) +
-                      tsk_carver::bytes_for(nd, 1);
-  if ((st = tsk_ws_require(ctx, need))) return st;
+  if ((st = tsk_ws_require(ctx, tsk_carver::bytes_for(nstat, 8)))) return st;
   tsk_carver cv(ctx->ws);
   double* stv = cv.take<double>(nstat);
-  float* d_R = cv.take<float>(static_cast<size_t>(nd) * k);
-  int8_t* d_op = cv.take<int8_t>(nd);
-  TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_R, R_rows_host, sizeof(float) * nd * k, cudaMemcpyHostToDevice, ctx->stream));
-  TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_op, op_host, nd, cudaMemcpyHostToDevice, ctx->stream));
+  // the projection rows and signs go through the layout cache (no copy when a
+  // call with the same rows was made before, e.g. before graph capture)
+  std::string key = "upd";
+  append(key, &nd, 1);
+  append(key, &k, 1);
+  append(key, R_rows_host, static_cast<size_t>(nd) * k);
+  append(key, op_host, nd);
+  const Blob* ub = blob_get(ctx, key, [&](std::vector<char>& buf, std::vector<int64_t>& meta) {
+    std::vector<float> rr(R_rows_host, R_rows_host + static_cast<size_t>(nd) * k);
+    std::vector<int8_t> oo(op_host, op_host + nd);
+    meta = {static_cast<int64_t>(put(buf, rr)), static_cast<int64_t>(put(buf, oo))};
+  }, &st);
+  if (!ub) return st;
+  const float* d_R = reinterpret_cast<const float*>(static_cast<char*>(ub->dev) + ub->meta[0]);
+  const int8_t* d_op = reinterpret_cast<const int8_t*>(static_cast<char*>(ub->dev) + ub->meta[1]);
   if ((st = tsk_launch_colstats(ctx, T_dims, t_dtype, L.soff, L.slen, static_cast<int64_t>(n_series) * nd, stv))) return st;
   if ((st = tsk_launch_update_dims(ctx, S, T_dims, t_dtype, n_series, L.cum, L.len, L.total_samples, nd, d_R, d_op, k,
                                    precision, stv)))

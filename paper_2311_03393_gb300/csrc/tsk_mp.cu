@@ -698,6 +698,32 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
   I[e] = j;
 }
 
+// Raise a kernel's dynamic shared-memory limit once per (device, kernel), and
+// only when a larger size is needed, so calls captured in a CUDA graph issue
+// no attribute changes.
+template <typename K>
+cudaError_t set_smem_limit(K kernel, int device, int bytes, int /*slot*/) {
+  struct Entry {
+    int device;
+    const void* fn;
+    int bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> done;
+  std::lock_guard<std::mutex> lock(mu);
+  const void* fn = reinterpret_cast<const void*>(kernel);
+  for (auto& e : done)
+    if (e.device == device && e.fn == fn) {
+      if (bytes <= e.bytes) return cudaSuccess;
+      const cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (r == cudaSuccess) e.bytes = bytes;
+      return r;
+    }
+  const cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (r == cudaSuccess) done.push_back({device, fn, bytes});
+  return r;
+}
+
 template <typename TX>
 tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_plan& plan, int32_t m, int32_t excl,
                      int32_t precision, void* P, int32_t* I, char* ws) {
@@ -725,7 +751,7 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
   if (f64) TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.bidx, 0x7f, sizeof(int32_t) * W, st));  // ~INT_MAX
   if (plan.total_chunks > 0) {
     const size_t smem = sizeof(double) * 2 * (kWinChunk + m + 2);
-    TSK_CUDA_TRY(ctx, cudaFuncSetAttribute(k_window_stats<TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    TSK_CUDA_TRY(ctx, set_smem_limit(k_window_stats<TX>, ctx->device, static_cast<int>(smem), 0));
     k_window_stats<TX><<<static_cast<unsigned>(plan.total_chunks), kWinThreads, smem, st>>>(
         X, plan.xoff, plan.len, plan.woff, plan.chunk_prefix, n_streams, m, f64 ? 1 : 0, wa, ctx->d_err);
     TSK_LAUNCH_CHECK(ctx, "k_window_stats");
@@ -755,8 +781,7 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
       }
     } else {
       const size_t smem = sizeof(MpWarpSmem) * kWarps;
-      TSK_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mp_diag<TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem)));
+      TSK_CUDA_TRY(ctx, set_smem_limit(k_mp_diag<TX>, ctx->device, static_cast<int>(smem), 1));
       int per_sm = 0;
       TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<TX>, kWarps * 32, smem));
       per_sm = std::max(per_sm, 1);
