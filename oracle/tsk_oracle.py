@@ -13,6 +13,10 @@ Time Series for Fast Discord Mining" (arXiv 2311.03393) defines:
   * Sec. III-A global z-normalisation of every stream, then the sketch of
                Alg. 1 (count sketch), written as S = R^T T_bar for a (d, k) R
   * Alg. 2     time detection: per sketch stream MP discord, keep the best group
+  * Alg. 3     dimension detection: for the discord window i* of group g*,
+               the 1NN distance of that window in every raw stream j of the
+               group J_g*, keep the largest; then the optional refinement
+               (a whole self-join profile of the chosen stream)
   * Sec. III-C dimension addition/deletion by linearity of the sketch
   * the adjoint of the top-K aggregated discord scores (not in the paper; the
     derivative of the same definitions, checked against central differences)
@@ -30,6 +34,13 @@ Readings where the paper is silent (the same readings the CUDA path takes):
     dist(const, non-const) = sqrt(m).
   * ties: lowest neighbour index j, lowest discord index i, lowest group g.
   * top-K: repeat argmax, then mask |i - i*| < topk_excl (default m).
+  * Alg. 3: J_g = {j : R[j, g] != 0} (the dimensions a count sketch hashes
+    to g; every dimension for a dense Gaussian R).  Self-join form: the
+    score of stream j is the self-join profile value of window i* in T_j.
+    j* = the first j (ascending) with a score above every earlier one,
+    starting from 0; when no score exceeds 0, the lowest j of J_g* (score 0);
+    an empty J_g* gives j* = -1.  Refinement = the top-1 discord of T_j*'s
+    own self-join profile.
   * bf16-matched sketch: T_bar and R are rounded to bfloat16 (round to nearest,
     ties to even, from the float64 value) before the float64 sum.
 """
@@ -347,3 +358,52 @@ def cells(n: int, m: int, excl: int) -> int:
     l = n - m + 1
     e = l - excl
     return max(0, e) * max(0, e + 1) // 2
+
+
+# ---------------------------------------------------------------------------
+# Alg. 3: discord dimension detection (second phase) and its refinement
+# ---------------------------------------------------------------------------
+
+def dim_groups(R) -> list:
+    """J_g for every sketch stream g: the dimensions j with R[j, g] != 0 (Sec. III-C, Alg. 3 input)."""
+    R = np.asarray(R)
+    return [np.flatnonzero(R[:, g] != 0) for g in range(R.shape[1])]
+
+
+def dimension_detection(T, R, discords, m: int, excl: int) -> tuple:
+    """Alg. 3 for every discord (i*, g*) of the time-detection phase.
+
+    For j in J_g* (ascending), s^(j) and its neighbour are the self-join
+    profile value and index of window i* in raw stream T_j (Def. 6 at one
+    row).  Keep j* with s_bsf starting at 0 and a strict '>'.
+    Returns (picks, scores, nns): picks[r] = (j*, s^(j*), nn^(j*)), scores
+    and nns of shape (len(discords), d) with NaN / -1 outside J_g*.
+    """
+    T = np.asarray(T, dtype=np.float64)
+    d = T.shape[0]
+    groups = dim_groups(R)
+    picks = []
+    scores = np.full((len(discords), d), np.nan)
+    nns = np.full((len(discords), d), -1, dtype=np.int64)
+    for r, (i_star, g_star) in enumerate(discords):
+        J = groups[g_star]
+        s_bsf, j_star = 0.0, -1
+        for j in J:
+            P, I = mp_rows(T[j], m, excl, [i_star])
+            scores[r, j], nns[r, j] = P[0], I[0]
+            if P[0] > s_bsf:
+                s_bsf, j_star = P[0], int(j)
+        if j_star < 0 and len(J):
+            j_star = int(J[0])  # every score is 0
+        if j_star < 0:
+            picks.append((-1, math.nan, -1))
+        else:
+            picks.append((j_star, float(scores[r, j_star]), int(nns[r, j_star])))
+    return picks, scores, nns
+
+
+def refine_dimension(T, j: int, m: int, excl: int, topk_excl: int | None = None) -> tuple:
+    """Refinement after Alg. 3: the top-1 discord (i, score, nn) of stream j's own self-join profile."""
+    P, I = mp_selfjoin(np.asarray(T, dtype=np.float64)[j], m, excl)
+    (i, _, score, nn), = discord_topk(P[None, :], I[None, :], 1, m if topk_excl is None else topk_excl)
+    return i, score, nn

@@ -332,3 +332,109 @@ def test_cell_count_by_enumeration():
         l = n - m + 1
         brute = sum(1 for i in range(l) for j in range(i + 1, l) if j - i >= excl)
         assert o.cells(n, m, excl) == brute
+
+
+# ---------------------------------------------------------------------------
+# Alg. 3: dimension detection and its refinement
+# ---------------------------------------------------------------------------
+
+def _zscore_windows_scipy(x, m):
+    """Every length-m window z-scored by scipy (ddof 0); constant windows -> zeros."""
+    W = np.lib.stride_tricks.sliding_window_view(np.asarray(x, dtype=np.float64), m)
+    Z = np.zeros_like(W)
+    for t in range(W.shape[0]):
+        if np.ptp(W[t]) > 0:
+            Z[t] = scipy.stats.zscore(W[t])
+    return Z
+
+
+def _brute_row(x, m, excl, i):
+    """min over |t - i| >= excl of the direct z-normalised distance, lowest t on ties."""
+    Z = _zscore_windows_scipy(x, m)
+    best, arg = math.inf, -1
+    for t in range(Z.shape[0]):
+        if abs(t - i) < excl:
+            continue
+        dist = float(np.linalg.norm(Z[i] - Z[t]))
+        if dist < best:
+            best, arg = dist, t
+    return best, arg
+
+
+def test_dim_groups_follow_the_count_sketch_hashes():
+    d, k, seed = 40, 6, 11
+    h, _ = synth.count_sketch_hashes(d, k, seed)
+    groups = o.dim_groups(synth.count_sketch_R(d, k, seed))
+    for g in range(k):
+        assert list(groups[g]) == [j for j in range(d) if h[j] == g]
+    assert sum(len(J) for J in groups) == d
+    for J in o.dim_groups(synth.gaussian_R(d, k, seed)):
+        assert list(J) == list(range(d))
+
+
+def test_dimension_detection_recovers_the_planted_dimension():
+    """A noise burst planted in stream 4 of periodic streams: Alg. 2 finds its time, Alg. 3 its dimension."""
+    d, n, m, k, p = 6, 700, 40, 3, 350
+    rng = np.random.default_rng(5)
+    t = np.arange(n)
+    periods = [10, 20, 25, 50, 20, 10]           # every sum of these repeats with period 100
+    T = np.stack([rng.uniform(0.5, 2.0) * np.sin(2 * np.pi * t / q + rng.uniform(0, 2 * np.pi))
+                  for q in periods])
+    T[4, p:p + m] = rng.normal(0.0, 1.0, m)
+    excl = synth.default_excl(m)
+    R = synth.count_sketch_R(d, k, seed=8)
+    res, _, _, _ = o.sketched_discords(T, R, m, excl, 1, m)
+    i_star, g_star = res[0][0], res[0][1]
+    assert abs(i_star - p) <= m and R[4, g_star] != 0
+    picks, scores, nns = o.dimension_detection(T, R, [(i_star, g_star)], m, excl)
+    assert picks[0][0] == 4
+    for j in range(d):
+        if R[j, g_star] == 0:
+            assert math.isnan(scores[0, j]) and nns[0, j] == -1
+        else:
+            b, a = _brute_row(T[j], m, excl, i_star)
+            assert abs(scores[0, j] - b) <= 1e-9 * max(1.0, b)
+            # near-zero distances of the periodic streams may tie; the neighbour must still be a minimiser
+            Z = _zscore_windows_scipy(T[j], m)
+            assert abs(float(np.linalg.norm(Z[i_star] - Z[nns[0, j]])) - b) <= 1e-9 * max(1.0, b)
+            assert j != 4 or nns[0, j] == a
+
+
+def test_dimension_detection_tie_zero_and_empty_rules():
+    rng = np.random.default_rng(3)
+    n, m, excl = 300, 20, 5
+    y = np.cumsum(rng.normal(size=n))
+    per = np.tile(np.sin(2 * np.pi * np.arange(25) / 25), n // 25 + 1)[:n]
+    T = np.stack([per, y, np.cumsum(rng.normal(size=n)), y.copy(), per * 3.0 + 1.0])
+    R = np.zeros((5, 3))
+    R[[0, 1, 3], 0] = [1.0, -1.0, 1.0]   # J_0 = {0, 1, 3}: 1 and 3 identical
+    R[[0, 4], 1] = [1.0, 1.0]            # J_1 = {0, 4}: both periodic, every score 0
+    i = 120
+    picks, scores, _ = o.dimension_detection(T, R, [(i, 0), (i, 1), (i, 2)], m, excl)
+    assert scores[0, 0] < 1e-6 and scores[0, 1] == scores[0, 3] > 0
+    assert picks[0][0] == 1                                  # lowest j among the tied maxima
+    assert picks[1][0] == 0 and picks[1][1] < 1e-6           # no score above 0 -> lowest j of J
+    assert picks[2][0] == -1 and math.isnan(picks[2][1]) and picks[2][2] == -1  # empty group
+
+
+def test_dimension_detection_invariant_to_affine_maps_of_streams():
+    T, _ = synth.random_walks(4, 400, 30, 1, seed=9, dtype=np.float64)
+    R = synth.gaussian_R(4, 2, seed=1)
+    picks, scores, nns = o.dimension_detection(T, R, [(150, 0), (40, 1)], 30, 8)
+    T2 = T * np.array([[2.5], [-0.5], [1e-3], [7.0]]) + np.array([[3.0], [-100.0], [0.0], [1e4]])
+    picks2, scores2, nns2 = o.dimension_detection(T2, R, [(150, 0), (40, 1)], 30, 8)
+    assert [p[0] for p in picks] == [p[0] for p in picks2]
+    np.testing.assert_allclose(scores, scores2, rtol=1e-7)
+    np.testing.assert_array_equal(nns, nns2)
+
+
+def test_refinement_is_the_brute_force_discord_of_the_stream():
+    T, _ = synth.random_walks(3, 240, 20, 1, seed=13, dtype=np.float64, discord_streams=[1])
+    excl = 5
+    i, score, nn = o.refine_dimension(T, 1, 20, excl)
+    rows = [_brute_row(T[1], 20, excl, t) for t in range(240 - 20 + 1)]
+    best = max(range(len(rows)), key=lambda t: (rows[t][0], -t))
+    assert i == best and abs(score - rows[best][0]) <= 1e-9 * rows[best][0] and nn == rows[best][1]
+    # the refined score is at least the Alg. 3 score of any window of that stream
+    picks, _, _ = o.dimension_detection(T, np.ones((3, 1)), [(37, 0)], 20, excl)
+    assert score >= o.mp_rows(T[1], 20, excl, [37])[0][0]
