@@ -222,6 +222,48 @@ TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, const int32_t*
                                int32_t d, int32_t k, int32_t m, float* dT, float* dR);
 
 /*
+ * dimension_detection - Alg. 3 (Sec. III-C, "Detection", second phase): the
+ * raw dimension behind each discord found on the sketch.
+ *
+ * For discord r of series s (window i* = idx[s][r] in sketch stream
+ * g* = grp[s][r], as returned by discord_topk on the sketch profiles), the
+ * group is J_g* = {j : R[j][g*] != 0} (the dimensions a count sketch hashes to
+ * g*; every dimension for a dense R).  Each j in J_g* is scored by the 1NN
+ * distance of its own window i*:
+ *   s_j = min over |t - i*| >= excl of dist(T_j[i*:i*+m], T_j[t:t+m])
+ * (Def. 6 at one row, z-normalised distance, the constant-window and
+ * no-neighbour rules of mp_selfjoin), and
+ *   j* = the first j (ascending) with s_j above every earlier score, from 0;
+ *        the lowest j of J_g* when no score exceeds 0; -1 for an empty group.
+ * Each s_j is the exact distance of the window the scan chose (re-evaluated
+ * with compensated sums); the scan picks it in float32.
+ *   T          : device, batch layout of ts_sketch_build (d streams per series,
+ *                float32 or float64 per t_dtype).
+ *   R          : device float32 d x k (row-major), the sketch matrix.
+ *   idx, grp   : device int32 [n_series][K]; idx < 0 marks an empty slot.
+ *   dim, dim_nn: device int32 [n_series][K] outputs: j*, and s_j*'s neighbour.
+ *   dim_score  : device float64 [n_series][K] output: s_j* (NaN when j* = -1,
+ *                +inf when window i* has no admissible neighbour).
+ *   dim_scores : optional (NULL to skip) device float64 [n_series][K][d]:
+ *                every s_j, NaN for j outside J_g*.
+ *   T_sel      : optional (NULL to skip) device buffer of T's element type:
+ *                per series s, K streams of series_len_host[s] samples (the
+ *                layout ts_sketch_build gives S for k = K), stream r a copy of
+ *                T_j* for discord r (zeros when j* = -1), for the optional
+ *                refinement (mp_selfjoin over T_sel, then discord_topk with
+ *                group 1).
+ * Errors: TSK_ERR_INVALID_ARG for NULL required arrays, a bad dtype,
+ * m outside [2, 4096], excl < 1, K < 1, k < 1, d < 1 or a series shorter than
+ * m; nothing is issued then.  Out-of-range idx/grp entries are treated as
+ * empty slots.
+ */
+TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, int32_t t_dtype, int32_t n_series,
+                                       const int32_t* series_len_host, int32_t d, const float* R, int32_t k,
+                                       int32_t m, int32_t excl, int32_t K, const int32_t* idx, const int32_t* grp,
+                                       int32_t* dim, double* dim_score, int32_t* dim_nn, double* dim_scores,
+                                       void* T_sel);
+
+/*
  * mp_selfjoin_static - the matrix profile of ONE float32 stream, like
  * mp_selfjoin with precision TSK_MP_FP32, but without allocating any device
  * memory and without a context.  The paper has no counterpart; this entry

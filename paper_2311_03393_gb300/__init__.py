@@ -8,6 +8,7 @@ from .api import (  # noqa: F401
     DiscordScores,
     context,
     default_excl,
+    dimension_detection,
     discord_topk,
     exact_discords,
     launch_count,
@@ -16,6 +17,7 @@ from .api import (  # noqa: F401
     pack_batch,
     profile_enable,
     profile_read,
+    refine_dimensions,
     reserve,
     set_tile_rows,
     sketched_discords,

@@ -257,6 +257,54 @@ def exact_discords(T: torch.Tensor, series_len: Sequence[int], d: int, m: int, K
     return {"P": P, "I": I, "idx": idx, "grp": grp, "score": score, "nn": nn}
 
 
+def dimension_detection(T: torch.Tensor, R: torch.Tensor, series_len: Sequence[int], d: int, m: int, idx, grp,
+                        excl: int | None = None, all_scores: bool = False, gather: bool = False):
+    """Alg. 3: the raw dimension behind each sketch discord (idx, grp of discord_topk).
+
+    Returns {"dim", "score", "nn"} ([n_series, K]; score float64), plus
+    "scores" ([n_series, K, d], NaN outside the group) when all_scores and
+    "T_sel" (the chosen streams, packed like a K-stream sketch) when gather.
+    """
+    _need_cuda(T, R, idx, grp)
+    excl = default_excl(m) if excl is None else int(excl)
+    k = int(R.shape[1])
+    ns = len(series_len)
+    K = int(idx.shape[1])
+    dev = T.device
+    dim = torch.empty((ns, K), dtype=torch.int32, device=dev)
+    score = torch.empty((ns, K), dtype=torch.float64, device=dev)
+    nn = torch.empty((ns, K), dtype=torch.int32, device=dev)
+    scores = torch.empty((ns, K, d), dtype=torch.float64, device=dev) if all_scores else None
+    T_sel = torch.empty(sum(series_len) * K, dtype=T.dtype, device=dev) if gather else None
+    Rf = R if R.dtype == torch.float32 else R.float().contiguous()
+    lens, lp = _i32_array(series_len)
+    h = _ctx(dev)
+    N.check(N.lib().dimension_detection(h, _ptr(T), _dtype_code(T), ns, lp, d, _ptr(Rf), k, int(m), excl, K,
+                                        _ptr(idx), _ptr(grp), _ptr(dim), _ptr(score), _ptr(nn),
+                                        _ptr(scores) if all_scores else None, _ptr(T_sel) if gather else None),
+            h, "dimension_detection")
+    out = {"dim": dim, "score": score, "nn": nn}
+    if all_scores:
+        out["scores"] = scores
+    if gather:
+        out["T_sel"] = T_sel
+    return out
+
+
+def refine_dimensions(T_sel: torch.Tensor, series_len: Sequence[int], K: int, m: int, excl: int | None = None,
+                      topk_excl: int | None = None, mp_precision: str = "fp32"):
+    """The refinement after Alg. 3: the top-1 discord of each chosen stream's own self-join profile.
+
+    T_sel is dimension_detection(..., gather=True)["T_sel"]; returns
+    {"idx", "score", "nn"} of shape [n_series, K].
+    """
+    lens = [n for n in series_len for _ in range(K)]
+    P, I = mp_selfjoin(T_sel, lens, m, excl, precision=mp_precision)
+    idx, _, score, nn = discord_topk(P, I, lens, 1, m, 1, topk_excl)
+    ns = len(series_len)
+    return {"idx": idx.view(ns, K), "score": score.view(ns, K), "nn": nn.view(ns, K), "P": P, "I": I}
+
+
 class DiscordScores(torch.autograd.Function):
     """Top-K aggregated discord scores of the sketched path, differentiable in T and R.
 

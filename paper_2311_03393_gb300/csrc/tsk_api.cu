@@ -591,6 +591,50 @@ extern "C" TSK_API tsk_status discord_topk(tsk_ctx* ctx, const void* P, int32_t 
                          static_cast<char*>(ctx->ws), L.total_samples);
 }
 
+extern "C" TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, int32_t t_dtype, int32_t n_series,
+                                                  const int32_t* series_len_host, int32_t d, const float* R,
+                                                  int32_t k, int32_t m, int32_t excl, int32_t K, const int32_t* idx,
+                                                  const int32_t* grp, int32_t* dim, double* dim_score,
+                                                  int32_t* dim_nn, double* dim_scores, void* T_sel) {
+  tsk_status st = enter(ctx);
+  if (st) return st;
+  if (!T || !R || !idx || !grp || !dim || !dim_score || !dim_nn)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: required arrays must be non-NULL");
+  if (t_dtype != TSK_F32 && t_dtype != TSK_F64)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: bad t_dtype");
+  if (n_series < 1 || d < 1 || k < 1 || K < 1)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: need n_series, d, k, K >= 1");
+  if (m < 2 || m > 4096)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: need 2 <= m <= 4096 (got %d)", m);
+  if (excl < 1) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: excl must be >= 1");
+  if ((st = check_lens(ctx, n_series, series_len_host, m, "dimension_detection"))) return st;
+  BatchLayout L{};
+  if ((st = batch_layout(ctx, n_series, series_len_host, d, &L))) return st;
+  // scan items: (discord, stream, chunk of windows) per series
+  std::string key = "dims";
+  const int32_t hdr[3] = {n_series, d, K};
+  append(key, hdr, 3);
+  append(key, &m, 1);
+  append(key, series_len_host, n_series);
+  const int64_t W = tsk_dims_window_chunk();
+  const Blob* b = blob_get(ctx, key, [&](std::vector<char>& buf, std::vector<int64_t>& meta) {
+    std::vector<int64_t> pre(static_cast<size_t>(n_series) + 1, 0);
+    for (int s = 0; s < n_series; ++s) {
+      const int64_t l = static_cast<int64_t>(series_len_host[s]) - m + 1;
+      pre[s + 1] = pre[s] + static_cast<int64_t>(K) * d * ((l + W - 1) / W);
+    }
+    meta = {pre[n_series], 0};
+    meta[1] = static_cast<int64_t>(put(buf, pre));
+  }, &st);
+  if (!b) return st;
+  const int64_t total_items = b->meta[0];
+  const int64_t* item_prefix = reinterpret_cast<const int64_t*>(static_cast<char*>(b->dev) + b->meta[1]);
+  if ((st = tsk_ws_require(ctx, tsk_dims_ws_bytes(n_series, K, d)))) return st;
+  return tsk_launch_dims(ctx, T, t_dtype, n_series, L.cum, L.len, item_prefix, total_items, L.total_samples, d, R, k,
+                         m, excl, K, idx, grp, dim, dim_score, dim_nn, dim_scores, T_sel,
+                         static_cast<char*>(ctx->ws));
+}
+
 extern "C" TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, const int32_t* idx, const int32_t* grp,
                                           const int32_t* nn, int32_t K, const void* T, int32_t t_dtype,
                                           const double* stats, const float* R, const float* S, int32_t n_series,

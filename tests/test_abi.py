@@ -55,3 +55,9 @@ def test_null_context_is_rejected(libpath):
     lib = _native.lib()
     assert lib.ts_sketch_build(None, None, 0, 0, None, 0, None, 0, 0, None, None) == 1
     assert lib.mp_selfjoin(None, None, 0, 0, None, None, 0, 0, 0, None, None) == 1
+
+
+def test_dimension_detection_rejects_a_null_context(libpath):
+    lib = _native.lib()
+    assert lib.dimension_detection(None, None, 0, 0, None, 0, None, 0, 0, 0, 0, None, None, None, None, None,
+                                   None, None) == 1
