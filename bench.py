@@ -4,6 +4,7 @@
 One step is one pass of the whole path over one batch of synthetic input:
   sketch build (global z-normalisation + S = R^T T_bar, bfloat16 tensor cores)
   -> matrix profile of the k sketch streams -> aggregation + top-K discords
+  -> the dimension of each discord (Alg. 3 over the discord's sketch group)
   -> adjoint of the discord scores
   -> delete one dimension (rank-one update) -> re-profile the changed sketch
      streams -> top-K
@@ -266,8 +267,9 @@ def run_gpu(args):
         tsk.ts_sketch_build(Tin, R, lens, d, precision="bf16", out=S, stats=stats)
         Ps, Is = tsk.mp_selfjoin(S, slen_k, m, excl, P=bufs["s"][0], I=bufs["s"][1])
         top_s = tsk.discord_topk(Ps, Is, lens, k, m, K)
-        mark(1)
         idx, grp, score, nn = top_s
+        dims = tsk.dimension_detection(Tin, R, lens, d, m, idx, grp, excl)
+        mark(1)
         tsk.mp_backward(dscore, idx, grp, nn, Tin, stats, R, S, lens, d, m)
         mark(2)
         dirty, _ = tsk.ts_sketch_update_dims(S, Tdel, lens, R_del, [-1])
@@ -278,12 +280,12 @@ def run_gpu(args):
         Pe, Ie = tsk.mp_selfjoin(Tin, slen_d, m, excl, P=bufs["e"][0], I=bufs["e"][1])
         top_e = tsk.discord_topk(Pe, Ie, lens, d, m, K)
         mark(4)
-        return top_s, top_u, top_e, dirty
+        return top_s, top_u, top_e, dirty, dims
 
     cps = sum(cells_per_stream(n, m, excl) for n in lens)
     l0 = tsk.launch_count()
     for _ in range(args.warmup):
-        _, _, _, dirty = step(T)
+        _, _, _, dirty, _ = step(T)
     torch.cuda.synchronize()
     launches_per_step = (tsk.launch_count() - l0) // max(1, args.warmup)
     n_dirty = int(np.sum(dirty))
@@ -304,6 +306,7 @@ def run_gpu(args):
     tsk.profile_enable(True)
     tsk.profile_read("mp_diag")
     tsk.profile_read("sketch")
+    tsk.profile_read("dims")
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -326,6 +329,7 @@ def run_gpu(args):
     tsk.profile_enable(False)
     mp_ms, mp_launches = tsk.profile_read("mp_diag")
     sk_ms, sk_launches = tsk.profile_read("sketch")
+    dd_ms, dd_launches = tsk.profile_read("dims")
     part = np.array([[ev[s][i].elapsed_time(ev[s][i + 1]) for i in range(4)] for s in range(args.steps)])
     step_ms = part.sum(axis=1)
     t_max, cells_sum = dist.reduce_max_sum(float(step_ms.sum()), float(cells_step * args.steps))
@@ -335,7 +339,7 @@ def run_gpu(args):
     # --- end to end through the public API: pinned host T in, discords out
     e2e = None
     if not args.no_e2e:
-        out_host = torch.empty(3 * 4 * K * ns, dtype=torch.float32).pin_memory()
+        out_host = torch.empty((3 * 4 + 2) * K * ns, dtype=torch.float32).pin_memory()
         h2d = T_host.numel() * 4
         d2h = out_host.numel() * 4
         Tdev = torch.empty_like(T)
@@ -346,9 +350,10 @@ def run_gpu(args):
             Tdev.copy_(T_host, non_blocking=True)
             Tdel_dev.copy_(torch.cat([Tdev[int(off[s]) + del_dim * n: int(off[s]) + (del_dim + 1) * n]
                                       for s, n in enumerate(lens)]))
-            top_s, top_u, top_e, _ = step(Tdev, Tdel=Tdel_dev)
+            top_s, top_u, top_e, _, dims = step(Tdev, Tdel=Tdel_dev)
             res = torch.cat([torch.stack([t[1].float().ravel(), t[0].float().ravel(), t[2].float().ravel(),
-                                          t[3].float().ravel()]).ravel() for t in (top_s, top_u, top_e)])
+                                          t[3].float().ravel()]).ravel() for t in (top_s, top_u, top_e)] +
+                            [dims["dim"].float().ravel(), dims["score"].float().ravel()])
             out_host.copy_(res, non_blocking=True)
 
         for _ in range(2):
@@ -406,11 +411,13 @@ def run_gpu(args):
                                    f"({peak_kind} max clock); 4 FMA-pipe ops per cell",
                      "ms_per_launch": mp_ms / mp_launches if mp_launches else None},
         "sketch_kernel": sketch_info,
+        "dims_kernel": ({"kernel": "k_dd_scan", "ms_per_launch": dd_ms / dd_launches} if dd_launches else None),
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": e2e,
     }
     if graph is None:
+        # sketched mining = sketch + profiles + top-K (Alg. 2) + dimension detection (Alg. 3)
         line["parts_ms"] = {"sketched_mining": parts[0], "adjoint": parts[1], "dim_update_and_reprofile": parts[2],
                             "exact_mining": parts[3]}
         line["speedup_exact_over_sketched"] = parts[3] / parts[0] if parts[0] > 0 else None

@@ -111,7 +111,7 @@ TSK_API int64_t tsk_launch_count(const tsk_ctx* ctx);
  * stream around every launch of the named kernels (not during graph capture).
  * tsk_profile_read waits for them, returns the summed device time and the
  * launch count since the last read, and clears them. */
-enum { TSK_PROF_MP_DIAG = 0, TSK_PROF_SKETCH = 1, TSK_PROF_COUNT = 2 };
+enum { TSK_PROF_MP_DIAG = 0, TSK_PROF_SKETCH = 1, TSK_PROF_DIMS = 2, TSK_PROF_COUNT = 3 };
 TSK_API tsk_status tsk_profile_enable(tsk_ctx* ctx, int32_t enable);
 TSK_API tsk_status tsk_profile_read(tsk_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches);
 

@@ -20,7 +20,7 @@ STATUS_NAMES = {
 TSK_F32, TSK_F64 = 0, 1
 TSK_SKETCH_BF16, TSK_SKETCH_FP32, TSK_SKETCH_FP64 = 0, 1, 2
 TSK_MP_FP32, TSK_MP_FP64 = 0, 1
-TSK_PROF_MP_DIAG, TSK_PROF_SKETCH = 0, 1
+TSK_PROF_MP_DIAG, TSK_PROF_SKETCH, TSK_PROF_DIMS = 0, 1, 2
 
 # name -> (restype, argtypes), mirroring include/tsketch.h
 _P = C.c_void_p

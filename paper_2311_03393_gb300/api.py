@@ -205,11 +205,11 @@ def profile_enable(on: bool = True, device=None) -> None:
 
 
 def profile_read(kernel: str = "mp_diag", device=None) -> tuple:
-    """(total device ms, launches) of `kernel` ('mp_diag' or 'sketch') since the last read."""
+    """(total device ms, launches) of `kernel` ('mp_diag', 'sketch' or 'dims') since the last read."""
     h = context(device)
     ms = C.c_double()
     n = C.c_int64()
-    kid = {"mp_diag": N.TSK_PROF_MP_DIAG, "sketch": N.TSK_PROF_SKETCH}[kernel]
+    kid = {"mp_diag": N.TSK_PROF_MP_DIAG, "sketch": N.TSK_PROF_SKETCH, "dims": N.TSK_PROF_DIMS}[kernel]
     N.check(N.lib().tsk_profile_read(h, kid, C.byref(ms), C.byref(n)), h, "tsk_profile_read")
     return float(ms.value), int(n.value)
 

@@ -610,9 +610,9 @@ extern "C" TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, i
   if ((st = check_lens(ctx, n_series, series_len_host, m, "dimension_detection"))) return st;
   BatchLayout L{};
   if ((st = batch_layout(ctx, n_series, series_len_host, d, &L))) return st;
-  // scan items: (discord, stream, chunk of windows) per series
+  // scan items: (stream, chunk of windows) per series
   std::string key = "dims";
-  const int32_t hdr[3] = {n_series, d, K};
+  const int32_t hdr[3] = {n_series, d, static_cast<int32_t>(tsk_dims_window_chunk())};
   append(key, hdr, 3);
   append(key, &m, 1);
   append(key, series_len_host, n_series);
@@ -621,7 +621,7 @@ extern "C" TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, i
     std::vector<int64_t> pre(static_cast<size_t>(n_series) + 1, 0);
     for (int s = 0; s < n_series; ++s) {
       const int64_t l = static_cast<int64_t>(series_len_host[s]) - m + 1;
-      pre[s + 1] = pre[s] + static_cast<int64_t>(K) * d * ((l + W - 1) / W);
+      pre[s + 1] = pre[s] + static_cast<int64_t>(d) * ((l + W - 1) / W);
     }
     meta = {pre[n_series], 0};
     meta[1] = static_cast<int64_t>(put(buf, pre));
@@ -629,7 +629,7 @@ extern "C" TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, i
   if (!b) return st;
   const int64_t total_items = b->meta[0];
   const int64_t* item_prefix = reinterpret_cast<const int64_t*>(static_cast<char*>(b->dev) + b->meta[1]);
-  if ((st = tsk_ws_require(ctx, tsk_dims_ws_bytes(n_series, K, d)))) return st;
+  if ((st = tsk_ws_require(ctx, tsk_dims_ws_bytes(n_series, K, d, m)))) return st;
   return tsk_launch_dims(ctx, T, t_dtype, n_series, L.cum, L.len, item_prefix, total_items, L.total_samples, d, R, k,
                          m, excl, K, idx, grp, dim, dim_score, dim_nn, dim_scores, T_sel,
                          static_cast<char*>(ctx->ws));

@@ -8,19 +8,23 @@
 // one, starting from 0.
 //
 // Pipeline per call:
-//   1. k_dd_scan    one CTA per (series, discord, stream, chunk of 1024 windows):
-//                   the distance profile of the query window i* against the
-//                   chunk.  The chunk is staged in shared memory shifted by its
-//                   first sample, window means and norms come from float64
-//                   chunk-local prefix sums, and each thread forms 4 consecutive
-//                   sliding dot products with the centred query in float32
-//                   (16 FMAs per 2 vector loads).  The largest correlation and
-//                   lowest window index merge per (series, discord, stream) in
-//                   a packed 64-bit word with atomicMax.
-//   2. k_dd_select  one warp per (series, discord): the chosen window of every
+//   1. k_dd_query   one warp per (series, discord, stream of its group): the
+//                   discord window centred in float64, stored in float32, with
+//                   its norm, sum and constant flag.
+//   2. k_dd_scan    one CTA per (series, stream, chunk of 2048 windows), for every
+//                   discord whose group holds the stream.  The chunk is staged in
+//                   shared memory shifted by its first sample; window means and
+//                   norms come from float-float prefix sums (no float64 on the
+//                   hot path: the FP64 pipe runs at 1/64 of FP32); each thread
+//                   forms 8 consecutive sliding dot products with the centred
+//                   query in float32 (32 FMAs per vector load, padded staging so
+//                   the loads are free of bank conflicts).  The largest
+//                   correlation and lowest window index merge per (series,
+//                   discord, stream) in a packed 64-bit word with atomicMax.
+//   3. k_dd_select  one warp per (series, discord): the chosen window of every
 //                   stream of the group is re-evaluated exactly (compensated
 //                   sums), then the strict running maximum over ascending j.
-//   3. k_dd_gather  (optional) copies stream j* of every discord into a
+//   4. k_dd_gather  (optional) copies stream j* of every discord into a
 //                   contiguous buffer for a self-join refinement profile.
 #include "tsk_internal.cuh"
 #include "tsk_rho.cuh"
@@ -30,8 +34,9 @@
 
 namespace {
 
-constexpr int kTW = 1024;          // windows per scan item
-constexpr int kScanThreads = 256;  // 4 windows per thread
+constexpr int kScanThreads = 256;
+constexpr int kWinPerThread = 8;                      // consecutive windows per thread
+constexpr int kTW = kScanThreads * kWinPerThread;     // 2048 windows per scan item
 constexpr double kConstRelVar = 1e-12;
 
 struct DimArgs {
@@ -42,187 +47,303 @@ struct DimArgs {
   const int32_t* idx;          // n_series x K
   const int32_t* grp;          // n_series x K
   unsigned long long* best;    // n_series x K x d
-  int n_series, d, k, m, excl, K;
+  float* Q;                    // n_series x K x d x m4: centred queries
+  float4* qinfo;               // n_series x K x d: {1/||q||, sum(q), active, constant}
+  int n_series, d, k, m, m4, excl, K;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(TSK_FULL_MASK, v, o);
-  return v;
+// ---- float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi)/2) ----
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ FF ff_fast(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = ff_two_sum(a.h, b.h);
+  return ff_fast(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ FF ff_sqr(FF a) {
+  const float p = __fmul_rn(a.h, a.h);
+  const float e = __fmaf_rn(a.h, a.h, -p);
+  return ff_fast(p, __fmaf_rn(__fmul_rn(2.0f, a.h), a.l, e));
+}
+__device__ __forceinline__ FF ff_mul(FF a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  const float e = __fmaf_rn(a.h, b, -p);
+  return ff_fast(p, __fmaf_rn(a.l, b, e));
+}
+// x - x_ref as float-float: exact for float samples (two-sum), rounded to ~2^-48 for double samples
+__device__ __forceinline__ FF ff_shift(float x, float xr) { return ff_two_sum(x, -xr); }
+__device__ __forceinline__ FF ff_shift(double x, double xr) {
+  const double y = x - xr;
+  const float h = static_cast<float>(y);
+  return {h, static_cast<float>(y - static_cast<double>(h))};
+}
+__device__ __forceinline__ FF ff_shfl_up(FF v, int o) {
+  return {__shfl_up_sync(TSK_FULL_MASK, v.h, o), __shfl_up_sync(TSK_FULL_MASK, v.l, o)};
+}
+__device__ __forceinline__ FF ff_shfl(FF v, int lane) {
+  return {__shfl_sync(TSK_FULL_MASK, v.h, lane), __shfl_sync(TSK_FULL_MASK, v.l, lane)};
 }
 
-// Sum over the block (256 threads); every thread receives the total.
-__device__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int q = 0; q < kScanThreads / 32; ++q) t += red[q];
-  return t;
-}
+// padded staging index: 4 spare floats after every 32, so that lanes reading
+// float4s 32 bytes apart fall in distinct bank groups
+__device__ __forceinline__ int xs_phys(int p) { return p + ((p >> 5) << 2); }
 
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 
+// One warp per (series, discord, stream): the discord window of the stream,
+// centred in float64 and stored as float32, with its norm, sum and constant flag.
+template <typename TX>
+__global__ void __launch_bounds__(256) k_dd_query(const TX* __restrict__ T, DimArgs a) {
+  const int64_t wid = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = static_cast<int64_t>(a.n_series) * a.K * a.d;
+  if (wid >= total) return;
+  const int j = static_cast<int>(wid % a.d);
+  const int64_t sr = wid / a.d;
+  const int s = static_cast<int>(sr / a.K);
+  const int n = a.len[s];
+  const int l = n - a.m + 1;
+  const int i_star = a.idx[sr];
+  const int g_star = a.grp[sr];
+  const bool active = i_star >= 0 && i_star < l && g_star >= 0 && g_star < a.k &&
+                      a.R[static_cast<int64_t>(j) * a.k + g_star] != 0.f;
+  if (!active) {
+    if (lane == 0) a.qinfo[wid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const TX* x = T + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n + i_star;
+  double sum = 0.0;
+  for (int t = lane; t < a.m; t += 32) sum += static_cast<double>(x[t]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(TSK_FULL_MASK, sum, o);
+  const double mu = sum / a.m;
+  double var = 0.0, sq = 0.0, nq = 0.0;
+  float* q = a.Q + wid * a.m4;
+  for (int t = lane; t < a.m4; t += 32) {
+    float v = 0.f;
+    if (t < a.m) {
+      const double dv = static_cast<double>(x[t]) - mu;
+      var += dv * dv;
+      v = static_cast<float>(dv);
+    }
+    q[t] = v;
+    sq += static_cast<double>(v);
+    nq += static_cast<double>(v) * static_cast<double>(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    var += __shfl_xor_sync(TSK_FULL_MASK, var, o);
+    sq += __shfl_xor_sync(TSK_FULL_MASK, sq, o);
+    nq += __shfl_xor_sync(TSK_FULL_MASK, nq, o);
+  }
+  const bool q_const = (var / a.m) <= kConstRelVar * fmax(1.0, mu * mu);
+  if (lane == 0)
+    a.qinfo[wid] = make_float4(nq > 0.0 ? static_cast<float>(1.0 / sqrt(nq)) : 0.f, static_cast<float>(sq), 1.f,
+                               q_const ? 1.f : 0.f);
+}
+
+// One CTA per (series, stream, chunk of 2048 windows), for every discord whose
+// group holds the stream.  See the file comment.
 template <typename TX>
 __global__ void __launch_bounds__(kScanThreads) k_dd_scan(const TX* __restrict__ T, DimArgs a, int64_t total_items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
-  const int m4 = (m + 3) & ~3;
-  const int xs_len = kTW + m4 + 8;                   // staged samples (zero padded)
-  float* xs = reinterpret_cast<float*>(smem_raw);     // [xs_len]
-  float* qs = xs + xs_len;                            // [m4]
-  double* p1 = reinterpret_cast<double*>(qs + m4 + ((m4 & 1) ? 1 : 0));  // [kTW + m] prefix of shifted samples
-  double* p2 = p1 + (kTW + m);                        // [kTW + m] prefix of their squares
-  __shared__ double red[kScanThreads / 32];
-  __shared__ double seg1[kScanThreads], seg2[kScanThreads];
+  const int m4 = a.m4;
+  const int ns_max = kTW + m4 + 8;                             // staged samples (zero padded)
+  float* xs = reinterpret_cast<float*>(smem_raw);              // [xs_phys(ns_max)]
+  const int xs_words = xs_phys(ns_max) + 4;
+  float* qs = xs + xs_words;                                   // [m4]
+  float* w_inv = qs + m4;                                      // [kTW] 1/||window - mean|| (0: constant)
+  float* w_mean = w_inv + kTW;                                 // [kTW] window mean of the shifted samples
+  float* p1h = w_mean + kTW;                                   // [kTW + m] prefix of shifted samples (float-float)
+  float* p1l = p1h + (kTW + m);
+  float* p2h = p1l + (kTW + m);                                // [kTW + m] prefix of their squares
+  float* p2l = p2h + (kTW + m);
+  __shared__ float segs[4][kScanThreads];
   __shared__ unsigned long long wbest[kScanThreads / 32];
+  const int tid = threadIdx.x;
 
   for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     const int s = tsk_find_segment<int64_t>(a.item_prefix, a.n_series, item);
     const int n = a.len[s];
     const int l = n - m + 1;
     const int chunks = (l + kTW - 1) / kTW;
-    int64_t rem = item - a.item_prefix[s];
+    const int64_t rem = item - a.item_prefix[s];
     const int c = static_cast<int>(rem % chunks);
-    rem /= chunks;
-    const int j = static_cast<int>(rem % a.d);
-    const int r = static_cast<int>(rem / a.d);
-    const int i_star = a.idx[s * a.K + r];
-    if (i_star < 0 || i_star >= l) continue;
-    const int g_star = a.grp[s * a.K + r];
-    if (g_star < 0 || g_star >= a.k || a.R[static_cast<int64_t>(j) * a.k + g_star] == 0.f) continue;
+    const int j = static_cast<int>(rem / chunks);
     const int t0 = c * kTW;
     const int nw = min(kTW, l - t0);
-    // this chunk holds no admissible window when it lies inside the exclusion zone
-    if (t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl) continue;
-    const TX* x = T + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n;
-
-    // ---- query: float64 mean and variance, centred float32 copy ----
-    double sq = 0.0;
-    for (int t = threadIdx.x; t < m; t += kScanThreads) sq += static_cast<double>(x[i_star + t]);
-    const double mu_q = block_sum(sq, red) / m;
-    double vq = 0.0, sqs = 0.0, nq = 0.0;
-    for (int t = threadIdx.x; t < m4; t += kScanThreads) {
-      float v = 0.f;
-      if (t < m) {
-        const double dv = static_cast<double>(x[i_star + t]) - mu_q;
-        vq += dv * dv;
-        v = static_cast<float>(dv);
+    // any discord of this series whose group holds stream j and whose exclusion zone leaves a window here
+    bool any = false;
+    for (int r = 0; r < a.K; ++r) {
+      const int64_t qi = (static_cast<int64_t>(s) * a.K + r) * a.d + j;
+      if (a.qinfo[qi].z != 0.f) {
+        const int i_star = a.idx[static_cast<int64_t>(s) * a.K + r];
+        if (!(t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl)) any = true;
       }
-      qs[t] = v;
-      sqs += static_cast<double>(v);
-      nq += static_cast<double>(v) * static_cast<double>(v);
     }
-    const double var_q = block_sum(vq, red) / m;
-    const double sum_qs = block_sum(sqs, red);
-    const double norm_qs = sqrt(block_sum(nq, red));
-    const bool q_const = var_q <= kConstRelVar * fmax(1.0, mu_q * mu_q);
+    if (!any) continue;
+    const TX* x = T + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n + t0;
 
-    // ---- chunk: samples shifted by the first one, float64 prefix sums ----
-    const double x_ref = static_cast<double>(x[t0]);
-    const int ns = nw + m - 1;                          // samples the chunk's windows touch
-    for (int p = threadIdx.x; p < xs_len; p += kScanThreads)
-      xs[p] = (p < ns) ? static_cast<float>(static_cast<double>(x[t0 + p]) - x_ref) : 0.f;
-    // segmented inclusive scan of (y, y^2), y = x - x_ref in float64, over ns samples
+    // ---- stage the chunk shifted by its first sample; float-float prefix sums ----
+    const TX x_ref = x[0];
+    const int ns = nw + m - 1;
+    for (int p = tid; p < ns_max; p += kScanThreads) xs[xs_phys(p)] = (p < ns) ? ff_shift(x[p], x_ref).h : 0.f;
     const int seg = (ns + kScanThreads - 1) / kScanThreads;
-    const int lo = threadIdx.x * seg, hi = min(ns, lo + seg);
-    double a1 = 0.0, a2 = 0.0;
+    const int lo = tid * seg, hi = min(ns, lo + seg);
+    FF a1{0.f, 0.f}, a2{0.f, 0.f};
     for (int p = lo; p < hi; ++p) {
-      const double y = static_cast<double>(x[t0 + p]) - x_ref;
-      a1 += y;
-      a2 += y * y;
+      const FF y = ff_shift(x[p], x_ref);
+      a1 = ff_add(a1, y);
+      a2 = ff_add(a2, ff_sqr(y));
+      p1h[p + 1] = a1.h; p1l[p + 1] = a1.l;
+      p2h[p + 1] = a2.h; p2l[p + 1] = a2.l;
     }
-    seg1[threadIdx.x] = a1;
-    seg2[threadIdx.x] = a2;
+    segs[0][tid] = a1.h; segs[1][tid] = a1.l; segs[2][tid] = a2.h; segs[3][tid] = a2.l;
     __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 256 segment totals by one warp
-      double c1 = 0.0, c2 = 0.0;
+    if (tid < 32) {  // exclusive scan of the 256 segment totals (float-float) by one warp
+      FF c1{0.f, 0.f}, c2{0.f, 0.f};
       for (int q = 0; q < kScanThreads / 32; ++q) {
-        const int u = q * 32 + threadIdx.x;
-        double v1 = seg1[u], v2 = seg2[u];
-        double i1 = v1, i2 = v2;
+        const int u = q * 32 + tid;
+        FF i1{segs[0][u], segs[1][u]}, i2{segs[2][u], segs[3][u]};
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const double t1 = __shfl_up_sync(TSK_FULL_MASK, i1, o), t2 = __shfl_up_sync(TSK_FULL_MASK, i2, o);
-          if (threadIdx.x >= o) { i1 += t1; i2 += t2; }
+          const FF t1 = ff_shfl_up(i1, o), t2 = ff_shfl_up(i2, o);
+          if (tid >= o) { i1 = ff_add(i1, t1); i2 = ff_add(i2, t2); }
         }
-        seg1[u] = c1 + i1 - v1;
-        seg2[u] = c2 + i2 - v2;
-        c1 += __shfl_sync(TSK_FULL_MASK, i1, 31);
-        c2 += __shfl_sync(TSK_FULL_MASK, i2, 31);
+        FF e1 = ff_shfl_up(i1, 1), e2 = ff_shfl_up(i2, 1);  // exclusive within the warp
+        if (tid == 0) { e1 = FF{0.f, 0.f}; e2 = FF{0.f, 0.f}; }
+        e1 = ff_add(c1, e1);
+        e2 = ff_add(c2, e2);
+        c1 = ff_add(c1, ff_shfl(i1, 31));
+        c2 = ff_add(c2, ff_shfl(i2, 31));
+        segs[0][u] = e1.h; segs[1][u] = e1.l; segs[2][u] = e2.h; segs[3][u] = e2.l;
       }
     }
     __syncthreads();
     {
-      double b1 = seg1[threadIdx.x], b2 = seg2[threadIdx.x];
-      if (threadIdx.x == 0) { p1[0] = 0.0; p2[0] = 0.0; }
+      const FF o1{segs[0][tid], segs[1][tid]}, o2{segs[2][tid], segs[3][tid]};
+      if (tid == 0) { p1h[0] = 0.f; p1l[0] = 0.f; p2h[0] = 0.f; p2l[0] = 0.f; }
       for (int p = lo; p < hi; ++p) {
-        const double y = static_cast<double>(x[t0 + p]) - x_ref;
-        b1 += y;
-        b2 += y * y;
-        p1[p + 1] = b1;
-        p2[p + 1] = b2;
+        const FF v1 = ff_add(o1, FF{p1h[p + 1], p1l[p + 1]});
+        const FF v2 = ff_add(o2, FF{p2h[p + 1], p2l[p + 1]});
+        p1h[p + 1] = v1.h; p1l[p + 1] = v1.l;
+        p2h[p + 1] = v2.h; p2l[p + 1] = v2.l;
       }
     }
     __syncthreads();
-
-    // ---- 4 sliding dot products per thread ----
-    const int w0 = threadIdx.x * 4;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    const float4* xs4 = reinterpret_cast<const float4*>(xs);
-    const float4* qs4 = reinterpret_cast<const float4*>(qs);
-    float4 A = xs4[threadIdx.x];
-    for (int kk = 0; kk < m4; kk += 4) {
-      const float4 B = xs4[threadIdx.x + (kk >> 2) + 1];
-      const float4 q = qs4[kk >> 2];
-      const float v[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        acc[u] = __fmaf_rn(q.x, v[u + 0], acc[u]);
-        acc[u] = __fmaf_rn(q.y, v[u + 1], acc[u]);
-        acc[u] = __fmaf_rn(q.z, v[u + 2], acc[u]);
-        acc[u] = __fmaf_rn(q.w, v[u + 3], acc[u]);
+    // ---- window statistics: D = m * sum(y^2) - sum(y)^2 = m^2 var ----
+    // A window whose D is within the prefix sums' rounding of the constant
+    // threshold is decided from its samples: all equal (constant), else the
+    // float64 two-pass variance.
+    const float fm = static_cast<float>(m);
+    const float m_ref = fm * static_cast<float>(x_ref);
+    const float sqrt_m = sqrtf(fm);
+    for (int w = tid; w < nw; w += kScanThreads) {
+      const FF s1 = ff_add(FF{p1h[w + m], p1l[w + m]}, ff_neg(FF{p1h[w], p1l[w]}));
+      const FF s2 = ff_add(FF{p2h[w + m], p2l[w + m]}, ff_neg(FF{p2h[w], p2l[w]}));
+      const FF D = ff_add(ff_mul(s2, fm), ff_neg(ff_sqr(s1)));
+      const float Df = D.h + D.l;
+      const float mmu = m_ref + s1.h;                         // m * window mean
+      const float thr = static_cast<float>(kConstRelVar) * fmaxf(fm * fm, mmu * mmu);
+      const float slack = 0x1p-30f * fm * (p2h[w + m] + p2h[w]);
+      float inv;
+      if (Df > thr + slack) {
+        inv = sqrt_m * rsqrtf(Df);
+      } else {
+        bool equal = true;
+        for (int t = 1; t < m && equal; ++t) equal = (x[w + t] == x[w]);
+        if (equal) {
+          inv = 0.f;
+        } else {
+          double mu = 0.0;
+          for (int t = 0; t < m; ++t) mu += static_cast<double>(x[w + t]);
+          mu /= m;
+          double v = 0.0;
+          for (int t = 0; t < m; ++t) {
+            const double dv = static_cast<double>(x[w + t]) - mu;
+            v += dv * dv;
+          }
+          inv = (v / m <= kConstRelVar * fmax(1.0, mu * mu)) ? 0.f : static_cast<float>(1.0 / sqrt(v));
+        }
       }
-      A = B;
+      w_inv[w] = inv;
+      w_mean[w] = s1.h / fm;
     }
-
-    // ---- correlations and the chunk's best (largest key, lowest index) ----
-    unsigned long long best = 0ull;
-    const float inv_q = (norm_qs > 0.0) ? static_cast<float>(1.0 / norm_qs) : 0.f;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int w = w0 + u;
-      const int t = t0 + w;
-      if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
-      const double s1 = p1[w + m] - p1[w], s2 = p2[w + m] - p2[w];
-      const double mean_y = s1 / m;
-      const double var = fmax(0.0, s2 / m - mean_y * mean_y);
-      const double mu_t = x_ref + mean_y;
-      const bool t_const = var <= kConstRelVar * fmax(1.0, mu_t * mu_t);
-      float key;
-      if (q_const) key = t_const ? 1.0f : 0.5f;       // dist 0 to a constant window, sqrt(m) otherwise
-      else if (t_const) key = 0.5f;                    // 2m(1 - 1/2) = m
-      else {
-        const float cov = acc[u] - static_cast<float>(mean_y * sum_qs);
-        const float inv_t = static_cast<float>(1.0 / sqrt(m * var));
-        key = fminf(1.0f, fmaxf(-1.0f, cov * inv_q * inv_t));
-      }
-      best = umax64(best, tsk_pack(key, t));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
-    if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long b = 0ull;
+
+    // ---- every discord whose group holds this stream ----
+    for (int r = 0; r < a.K; ++r) {
+      const int64_t sr = static_cast<int64_t>(s) * a.K + r;
+      const float4 qi = a.qinfo[sr * a.d + j];
+      if (qi.z == 0.f) continue;
+      const int i_star = a.idx[sr];
+      if (t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl) continue;
+      const float* qg = a.Q + (sr * a.d + j) * m4;
+      for (int t = tid; t < m4; t += kScanThreads) qs[t] = qg[t];
+      __syncthreads();
+      const int w0 = tid * kWinPerThread;
+      float acc[kWinPerThread];
 #pragma unroll
-      for (int q = 0; q < kScanThreads / 32; ++q) b = umax64(b, wbest[q]);
-      if (b) atomicMax(&a.best[(static_cast<int64_t>(s) * a.K + r) * a.d + j], b);
+      for (int u = 0; u < kWinPerThread; ++u) acc[u] = 0.f;
+      if (qi.w == 0.f) {  // dot products with the centred query (a constant query needs none)
+        float4 A = *reinterpret_cast<const float4*>(xs + xs_phys(w0));
+        float4 B = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + 4));
+        const float4* qs4 = reinterpret_cast<const float4*>(qs);
+        for (int kk = 0; kk < m4; kk += 4) {
+          const float4 C = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + kk + 8));
+          const float4 q = qs4[kk >> 2];
+          const float v[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+#pragma unroll
+          for (int u = 0; u < kWinPerThread; ++u) {
+            acc[u] = __fmaf_rn(q.x, v[u + 0], acc[u]);
+            acc[u] = __fmaf_rn(q.y, v[u + 1], acc[u]);
+            acc[u] = __fmaf_rn(q.z, v[u + 2], acc[u]);
+            acc[u] = __fmaf_rn(q.w, v[u + 3], acc[u]);
+          }
+          A = B;
+          B = C;
+        }
+      }
+      unsigned long long best = 0ull;
+#pragma unroll
+      for (int u = 0; u < kWinPerThread; ++u) {
+        const int w = w0 + u;
+        const int t = t0 + w;
+        if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
+        const float inv_t = w_inv[w];
+        float key;
+        if (qi.w != 0.f) key = (inv_t == 0.f) ? 1.0f : 0.5f;  // dist 0 to a constant window, sqrt(m) otherwise
+        else if (inv_t == 0.f) key = 0.5f;                     // 2m(1 - 1/2) = m
+        else {
+          const float cov = __fmaf_rn(-w_mean[w], qi.y, acc[u]);
+          key = fminf(1.0f, fmaxf(-1.0f, cov * qi.x * inv_t));
+        }
+        best = umax64(best, tsk_pack(key, t));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
+      if ((tid & 31) == 0) wbest[tid >> 5] = best;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long b = 0ull;
+#pragma unroll
+        for (int q = 0; q < kScanThreads / 32; ++q) b = umax64(b, wbest[q]);
+        if (b) atomicMax(&a.best[sr * a.d + j], b);
+      }
+      __syncthreads();  // qs and wbest are reused by the next discord
     }
-    __syncthreads();  // shared buffers are reused by the next item
   }
 }
 
@@ -331,15 +452,19 @@ __global__ void k_dd_gather(const TX* __restrict__ T, const int64_t* __restrict_
 
 size_t scan_smem_bytes(int m) {
   const int m4 = (m + 3) & ~3;
-  const size_t floats = static_cast<size_t>(kTW + m4 + 8) + m4 + ((m4 & 1) ? 1 : 0);
-  return floats * 4 + static_cast<size_t>(2) * (kTW + m) * 8 + 16;
+  const int ns_max = kTW + m4 + 8;
+  const size_t xs_words = static_cast<size_t>(ns_max + ((ns_max >> 5) << 2)) + 4;
+  return (xs_words + m4 + 2 * static_cast<size_t>(kTW) + 4 * static_cast<size_t>(kTW + m)) * sizeof(float);
 }
 
 template <typename TX>
 tsk_status run_dims(tsk_ctx* ctx, const TX* T, const DimArgs& a, int64_t total_items, int32_t* dim, double* dim_score,
                     int32_t* dim_nn, double* dim_scores, TX* T_sel, int64_t total_samples) {
   cudaStream_t st = ctx->stream;
-  TSK_CUDA_TRY(ctx, cudaMemsetAsync(a.best, 0, sizeof(unsigned long long) * static_cast<size_t>(a.n_series) * a.K * a.d, st));
+  const int64_t triples = static_cast<int64_t>(a.n_series) * a.K * a.d;
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(a.best, 0, sizeof(unsigned long long) * static_cast<size_t>(triples), st));
+  k_dd_query<TX><<<static_cast<unsigned>((triples * 32 + 255) / 256), 256, 0, st>>>(T, a);
+  TSK_LAUNCH_CHECK(ctx, "k_dd_query");
   const size_t smem = scan_smem_bytes(a.m);
   TSK_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dd_scan<TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem)));
@@ -347,6 +472,7 @@ tsk_status run_dims(tsk_ctx* ctx, const TX* T, const DimArgs& a, int64_t total_i
     int per_sm = 0;
     TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dd_scan<TX>, kScanThreads, smem));
     const int64_t grid = std::min<int64_t>(total_items, static_cast<int64_t>(std::max(per_sm, 1)) * ctx->sm_count);
+    tsk_prof_scope ps(ctx, TSK_PROF_DIMS);
     k_dd_scan<TX><<<static_cast<unsigned>(grid), kScanThreads, smem, st>>>(T, a, total_items);
     TSK_LAUNCH_CHECK(ctx, "k_dd_scan");
   }
@@ -380,8 +506,12 @@ tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_s
   a.R = R;
   a.idx = idx;
   a.grp = grp;
+  const size_t triples = static_cast<size_t>(n_series) * K * d;
+  a.m4 = (m + 3) & ~3;
   tsk_carver cv(ws);
-  a.best = cv.take<unsigned long long>(static_cast<size_t>(n_series) * K * d);
+  a.best = cv.take<unsigned long long>(triples);
+  a.Q = cv.take<float>(triples * a.m4);
+  a.qinfo = cv.take<float4>(triples);
   a.n_series = n_series;
   a.d = d;
   a.k = k;
@@ -395,6 +525,8 @@ tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_s
                          static_cast<float*>(T_sel), total_samples);
 }
 
-size_t tsk_dims_ws_bytes(int32_t n_series, int32_t K, int32_t d) {
-  return tsk_carver::bytes_for(static_cast<size_t>(n_series) * K * d, 8);
+size_t tsk_dims_ws_bytes(int32_t n_series, int32_t K, int32_t d, int32_t m) {
+  const size_t triples = static_cast<size_t>(n_series) * K * d;
+  return tsk_carver::bytes_for(triples, 8) + tsk_carver::bytes_for(triples * ((m + 3) & ~3), 4) +
+         tsk_carver::bytes_for(triples, 16);
 }

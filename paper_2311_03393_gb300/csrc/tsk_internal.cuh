@@ -198,7 +198,7 @@ tsk_status tsk_launch_topk(tsk_ctx* ctx, const void* P, int p_dtype, const int32
                            int64_t max_l);
 // Dimension detection (Alg. 3) and the gather of the chosen streams.
 int tsk_dims_window_chunk();
-size_t tsk_dims_ws_bytes(int32_t n_series, int32_t K, int32_t d);
+size_t tsk_dims_ws_bytes(int32_t n_series, int32_t K, int32_t d, int32_t m);
 tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_series, const int64_t* d_cum,
                            const int32_t* d_len, const int64_t* d_item_prefix, int64_t total_items,
                            int64_t total_samples, int32_t d, const float* R, int32_t k, int32_t m, int32_t excl,
