@@ -13,6 +13,9 @@ Time Series for Fast Discord Mining" (arXiv 2311.03393) defines:
   * Sec. III-A global z-normalisation of every stream, then the sketch of
                Alg. 1 (count sketch), written as S = R^T T_bar for a (d, k) R
   * Alg. 2     time detection: per sketch stream MP discord, keep the best group
+  * Def. 6     the AB-join profile (T_test != T_train): every test window's
+               1NN distance among all training windows, with no exclusion
+  * Alg. 2/3   in their AB-join form (test against train)
   * Alg. 3     dimension detection: for the discord window i* of group g*,
                the 1NN distance of that window in every raw stream j of the
                group J_g*, keep the largest; then the optional refinement
@@ -41,6 +44,9 @@ Readings where the paper is silent (the same readings the CUDA path takes):
     starting from 0; when no score exceeds 0, the lowest j of J_g* (score 0);
     an empty J_g* gives j* = -1.  Refinement = the top-1 discord of T_j*'s
     own self-join profile.
+  * AB join: train and test are each z-normalised over their own length
+    before sketching ("respectively", Sec. III-A), sketched with the same R;
+    every training window is a candidate (no exclusion), lowest j on ties.
   * bf16-matched sketch: T_bar and R are rounded to bfloat16 (round to nearest,
     ties to even, from the float64 value) before the float64 sum.
 """
@@ -370,12 +376,14 @@ def dim_groups(R) -> list:
     return [np.flatnonzero(R[:, g] != 0) for g in range(R.shape[1])]
 
 
-def dimension_detection(T, R, discords, m: int, excl: int) -> tuple:
+def dimension_detection(T, R, discords, m: int, excl: int, T_train=None) -> tuple:
     """Alg. 3 for every discord (i*, g*) of the time-detection phase.
 
     For j in J_g* (ascending), s^(j) and its neighbour are the self-join
     profile value and index of window i* in raw stream T_j (Def. 6 at one
-    row).  Keep j* with s_bsf starting at 0 and a strict '>'.
+    row) or, with T_train, the AB-join value of test window i* of T_j against
+    the training stream T_train[j].  Keep j* with s_bsf starting at 0 and a
+    strict '>'.
     Returns (picks, scores, nns): picks[r] = (j*, s^(j*), nn^(j*)), scores
     and nns of shape (len(discords), d) with NaN / -1 outside J_g*.
     """
@@ -389,7 +397,10 @@ def dimension_detection(T, R, discords, m: int, excl: int) -> tuple:
         J = groups[g_star]
         s_bsf, j_star = 0.0, -1
         for j in J:
-            P, I = mp_rows(T[j], m, excl, [i_star])
+            if T_train is None:
+                P, I = mp_rows(T[j], m, excl, [i_star])
+            else:
+                P, I = abjoin_rows(T[j], np.asarray(T_train, dtype=np.float64)[j], m, [i_star])
             scores[r, j], nns[r, j] = P[0], I[0]
             if P[0] > s_bsf:
                 s_bsf, j_star = P[0], int(j)
@@ -407,3 +418,53 @@ def refine_dimension(T, j: int, m: int, excl: int, topk_excl: int | None = None)
     P, I = mp_selfjoin(np.asarray(T, dtype=np.float64)[j], m, excl)
     (i, _, score, nn), = discord_topk(P[None, :], I[None, :], 1, m if topk_excl is None else topk_excl)
     return i, score, nn
+
+
+# ---------------------------------------------------------------------------
+# Def. 6 AB join (test against train) and Alg. 2 in that form
+# ---------------------------------------------------------------------------
+
+def abjoin_rows(a, b, m: int, rows) -> tuple:
+    """AB-join profile of test stream a against training stream b at the given test rows (Def. 6).
+
+    For each test window i: P[i] = min over every training window j of
+    ||z(a[i:i+m]) - z(b[j:j+m])||, I[i] = the lowest such argmin j.
+    """
+    Za, _, _, _ = znorm_windows(a, m)
+    Zb, _, _, _ = znorm_windows(b, m)
+    rows = np.asarray(rows, dtype=np.int64)
+    P = np.empty(len(rows))
+    I = np.empty(len(rows), dtype=np.int64)
+    for r, i in enumerate(rows):
+        d = np.sqrt(((Zb - Za[i]) ** 2).sum(axis=1))
+        j = int(np.argmin(d))
+        P[r], I[r] = d[j], j
+    return P, I
+
+
+def mp_abjoin(a, b, m: int) -> tuple:
+    """(P, I) for every test window of a against training stream b."""
+    return abjoin_rows(a, b, m, np.arange(len(a) - m + 1))
+
+
+def ab_discords(T_test, T_train, m: int, K: int, topk_excl: int, R=None, bf16: bool = False):
+    """Ranked discords of the test series against the training series (Def. 5 in AB form, Alg. 2).
+
+    With R: both series are z-normalised over their own length and sketched
+    with the same R (Sec. III-A, Alg. 1), and the k sketch streams are
+    AB-joined.  Without R: the exact d-dimensional form on the raw streams.
+    Returns (ranked list, P, I).
+    """
+    if R is None:
+        A = np.asarray(T_test, dtype=np.float64)
+        B = np.asarray(T_train, dtype=np.float64)
+    else:
+        A = sketch(global_znorm(T_test)[0], R, bf16)
+        B = sketch(global_znorm(T_train)[0], R, bf16)
+    Ps, Is = [], []
+    for g in range(A.shape[0]):
+        P, I = mp_abjoin(A[g], B[g], m)
+        Ps.append(P)
+        Is.append(I)
+    P, I = np.array(Ps), np.array(Is)
+    return discord_topk(P, I, K, topk_excl), P, I

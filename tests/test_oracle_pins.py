@@ -438,3 +438,64 @@ def test_refinement_is_the_brute_force_discord_of_the_stream():
     # the refined score is at least the Alg. 3 score of any window of that stream
     picks, _, _ = o.dimension_detection(T, np.ones((3, 1)), [(37, 0)], 20, excl)
     assert score >= o.mp_rows(T[1], 20, excl, [37])[0][0]
+
+
+# ---------------------------------------------------------------------------
+# Def. 6 AB join and Alg. 2 / Alg. 3 in their train/test form
+# ---------------------------------------------------------------------------
+
+def test_abjoin_against_brute_force_pairs():
+    rng = np.random.default_rng(41)
+    a = np.cumsum(rng.normal(size=37))
+    b = np.cumsum(rng.normal(size=29))
+    b[5:11] = 2.0                                    # constant training windows
+    m = 6
+    Za, Zb = _zscore_windows_scipy(a, m), _zscore_windows_scipy(b, m)
+    P, I = o.mp_abjoin(a, b, m)
+    for i in range(len(Za)):
+        dists = [float(np.linalg.norm(Za[i] - Zb[j])) for j in range(len(Zb))]
+        jb = min(range(len(dists)), key=lambda j: (dists[j], j))
+        assert abs(P[i] - dists[jb]) <= 1e-9 and I[i] == jb
+
+
+def test_abjoin_of_a_series_with_itself_is_zero_and_the_closest_pair_is_shared():
+    rng = np.random.default_rng(42)
+    x = np.cumsum(rng.normal(size=300))
+    P, I = o.mp_abjoin(x, x, 20)
+    assert np.all(P < 1e-6)
+    Z = _zscore_windows_scipy(x, 20)
+    assert all(np.linalg.norm(Z[i] - Z[I[i]]) < 1e-6 for i in range(0, len(P), 17))
+    # min over test rows of P_ab == min over training rows of P_ba (the same closest pair)
+    y = np.cumsum(rng.normal(size=250))
+    Pab, _ = o.mp_abjoin(x, y, 20)
+    Pba, _ = o.mp_abjoin(y, x, 20)
+    assert abs(Pab.min() - Pba.min()) <= 1e-9
+
+
+def test_ab_discord_finds_the_window_that_training_never_saw():
+    """Test = train everywhere but one replaced window: the AB discord (exact and sketched) is there."""
+    d, n, m, k, p = 5, 600, 30, 2, 333
+    rng = np.random.default_rng(43)
+    t = np.arange(n)
+    train = np.stack([np.sin(2 * np.pi * t / q + rng.uniform(0, 6)) for q in (15, 20, 25, 30, 50)])
+    test = train.copy()
+    test[3, p:p + m] = rng.normal(size=m)
+    res, P, _ = o.ab_discords(test, train, m, 1, m)
+    assert abs(res[0][0] - p) < m and res[0][1] == 3
+    R = synth.count_sketch_R(d, k, seed=2)
+    res_s, _, _ = o.ab_discords(test, train, m, 1, m, R=R)
+    assert abs(res_s[0][0] - p) < m and R[3, res_s[0][1]] != 0
+    picks, _, _ = o.dimension_detection(test, R, [(res_s[0][0], res_s[0][1])], m, 0, T_train=train)
+    assert picks[0][0] == 3
+
+
+def test_ab_identity_count_sketch_gives_the_exact_ab_profiles():
+    rng = np.random.default_rng(44)
+    d, m = 3, 16
+    train = np.cumsum(rng.normal(size=(d, 200)), axis=1)
+    test = np.cumsum(rng.normal(size=(d, 150)), axis=1)
+    R = np.diag([1.0, -1.0, 1.0])                     # k = d, h(j) = j
+    _, Ps, Is = o.ab_discords(test, train, m, 2, m, R=R)
+    _, Pe, Ie = o.ab_discords(test, train, m, 2, m)
+    np.testing.assert_allclose(Ps, Pe, rtol=1e-9, atol=1e-9)
+    np.testing.assert_array_equal(Is, Ie)
