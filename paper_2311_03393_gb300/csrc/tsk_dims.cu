@@ -18,8 +18,8 @@
 //                   hot path: the FP64 pipe runs at 1/64 of FP32); each thread
 //                   forms 8 consecutive sliding dot products with the centred
 //                   query in float32 (32 FMAs per vector load, padded staging so
-//                   the loads are free of bank conflicts).  The largest
-//                   correlation and lowest window index merge per (series,
+//                   the loads are free of bank conflicts).  The largest key
+//                   rho - 1 and lowest window index merge per (series,
 //                   discord, stream) in a packed 64-bit word with atomicMax.
 //   3. k_dd_select  one warp per (series, discord): the chosen window of every
 //                   stream of the group is re-evaluated exactly (compensated
@@ -324,11 +324,11 @@ __global__ void __launch_bounds__(kScanThreads) k_dd_scan(const TX* __restrict__
         if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
         const float inv_t = w_inv[w];
         float key;
-        if (qi.w != 0.f) key = (inv_t == 0.f) ? 1.0f : 0.5f;  // dist 0 to a constant window, sqrt(m) otherwise
-        else if (inv_t == 0.f) key = 0.5f;                     // 2m(1 - 1/2) = m
+        if (qi.w != 0.f) key = (inv_t == 0.f) ? 0.0f : -0.5f;  // rho 1 (dist 0) to a constant window, else 1/2
+        else if (inv_t == 0.f) key = -0.5f;                     // rho 1/2: 2m(1 - 1/2) = m
         else {
           const float cov = __fmaf_rn(-w_mean[w], qi.y, acc[u]);
-          key = fminf(1.0f, fmaxf(-1.0f, cov * qi.x * inv_t));
+          key = fminf(0.0f, fmaxf(-2.0f, __fmaf_rn(cov * qi.x, inv_t, -1.0f)));  // rho - 1
         }
         best = umax64(best, tsk_pack(key, t));
       }

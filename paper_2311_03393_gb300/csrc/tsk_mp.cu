@@ -11,22 +11,31 @@
 //   2. k_next_const     next constant window at or after each index (only for
 //                       streams that have constant windows).
 //   3. k_mp_diag        persistent, diagonal-banded kernel.  A warp owns a band
-//                       of 32*V diagonals and H rows; lane t walks diagonals
-//                       d0 + tV .. d0 + tV + V - 1 down the rows with the float32
+//                       of 512 diagonals (two half bands of 256 walked in
+//                       lockstep as float2 pairs) and a run of rows; lane t walks
+//                       8 diagonals of each half down the rows with the float32
 //                       recurrence, anchored exactly in float64 at the first row.
-//                       Each cell's correlation rho = c * inv_i * inv_j updates the
-//                       row maximum (reduced over lanes through shared memory) and
-//                       the column maximum (carried from lane to lane as the
-//                       band's columns slide).  Keys carry the in-lane diagonal
-//                       offset in their 4 low mantissa bits, so a max also knows
-//                       its argmax.  Results merge into a packed (key, index)
-//                       64-bit word per window with atomicMax.
+//                       Each cell's key rho - 1 (rho = c * inv_i * inv_j) updates
+//                       the row maximum (reduced over lanes through shared memory)
+//                       and the column maximum (carried from lane to lane as the
+//                       band's columns slide).  Keys carry the diagonal's offset
+//                       within its half band in their 8 low mantissa bits, so a
+//                       max also knows its argmax.  Results merge into a packed
+//                       (key, index) 64-bit word per window with atomicMax.
 //   4. k_mp_refine      for every window: its chosen neighbour's distance,
 //                       dist = sqrt(2 m (1 - rho)) with rho re-evaluated exactly
 //                       (compensated sums), plus the constant-window rules.
 // The float64 variant (k_mp_diag_f64) is exact: one thread per diagonal, a
 // first pass takes the float64 maximum per window, a second pass the lowest
 // index attaining it.
+//
+// AB join (Def. 6 with T_test != T_train): the streams are the n test streams
+// followed by their n training partners (samples of the two halves in two
+// buffers).  The same kernels run with a row side and a column side: rows of
+// test stream q against columns of training stream q on diagonals delta >= 0,
+// then rows of the training stream against columns of the test stream on
+// delta >= 1, with no exclusion zone; row maxima feed the row side's profile
+// and column maxima the column side's.
 #include "tsk_internal.cuh"
 #include "tsk_rho.cuh"
 
@@ -49,7 +58,8 @@ constexpr int kMaxWalk = 16384;          // rows walked from one float64 anchor 
 constexpr int kWinChunk = 1024;          // windows per window-stats CTA
 constexpr int kWinThreads = 256;
 constexpr int kPad = 2048;               // zeroed slack after each stream's window arrays
-constexpr float kEmpty = -3.0f;          // below every correlation
+constexpr float kEmpty = -3.0f;          // below every key (keys are rho - 1 >= -2)
+constexpr float kKeyFloor = -2.5f;       // keys above this are real cells
 constexpr double kConstRelVar = 1e-12;
 
 struct WinArrays {
@@ -64,6 +74,13 @@ struct WinArrays {
   double* inv64;   // float64 mode only
   int32_t* bidx;   // float64 mode only
 };
+
+// Samples of stream q: streams before `split` live in X, the rest in X2
+// (offsets continue across the two buffers).
+template <typename TX>
+__device__ __forceinline__ const TX* stream_base(const TX* X, const TX* X2, const int64_t* xoff, int split, int q) {
+  return q < split ? X + xoff[q] : X2 + (xoff[q] - xoff[split]);
+}
 
 // ---------------------------------------------------------------------------
 // 1. window statistics
@@ -88,7 +105,8 @@ __device__ __forceinline__ void block_excl_scan2(double& a, double& b, double* s
 }
 
 template <typename TX>
-__global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restrict__ X, const int64_t* __restrict__ xoff,
+__global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restrict__ X, const TX* __restrict__ X2,
+                                                              int split, const int64_t* __restrict__ xoff,
                                                               const int32_t* __restrict__ len,
                                                               const int64_t* __restrict__ woff,
                                                               const int64_t* __restrict__ chunk_prefix, int n_streams,
@@ -102,7 +120,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restri
   const int w0 = static_cast<int>(blockIdx.x - chunk_prefix[q]) * kWinChunk;
   const int nw = min(kWinChunk, l - w0);
   const int ns = min(n - w0, nw + m);  // samples w0 .. w0 + ns - 1
-  const TX* x = X + xoff[q];
+  const TX* x = stream_base(X, X2, xoff, split, q);
   const int64_t wb = woff[q];
   double* E1 = sm;             // E1[u] = sum of the first u shifted samples
   double* E2 = sm + (ns + 1);
@@ -216,13 +234,17 @@ __global__ void __launch_bounds__(kWinThreads) k_next_const(const int32_t* __res
 //   - 8 + 8 column maxima held in registers; as the rows advance the band's
 //     columns slide, the column leaving lane t passes to lane t-1 and the one
 //     leaving lane 0 is complete for this band.
-// A key is the correlation with its 8 low mantissa bits replaced by the
-// diagonal's offset within its half (8t + v), so maxima carry their argmax.
+// A key is rho - 1 (one FMA: t * inv_i - 1, exact to float32 relative
+// precision near rho = 1, where close matches are told apart) with its 8 low
+// mantissa bits replaced by the diagonal's offset within its half (8t + v), so
+// maxima carry their argmax; the tag then costs at most 2^-16 of 1 - rho.
 // Column data (df, dg, 1/norm) stream through a swizzled shared-memory ring
 // refilled 32 rows ahead; row data through a 32-row buffer of broadcast pairs.
 // ---------------------------------------------------------------------------
 struct MpArgs {
   const void* X;
+  const void* X2;              // AB join: samples of the training streams (streams >= split)
+  int split;                   // AB join: number of test streams (self-join: n_streams)
   const int64_t* xoff;
   const int32_t* len;
   const int64_t* woff;
@@ -272,7 +294,8 @@ __device__ __forceinline__ double ld_guard(const TX* __restrict__ x, int idx, in
 // Merge the 32 (or `count`) buffered rows and lane-0 column exits into the profile.
 // Buffer slot u belongs to row base + u and to columns base + u + d0 (+ 256).
 __device__ __forceinline__ void flush_chunk(MpWarpSmem& w, int count, int base, int d0, int l,
-                                            unsigned long long* __restrict__ best, int lane) {
+                                            unsigned long long* __restrict__ best,
+                                            unsigned long long* __restrict__ bestc, int lane) {
   __syncwarp();
   if (lane < count) {
     const int ir = base + lane;
@@ -286,29 +309,38 @@ __device__ __forceinline__ void flush_chunk(MpWarpSmem& w, int count, int base, 
     }
     const bool useb = mb > ma;
     const float bk = useb ? mb : ma;
-    if (bk > -2.f) {
+    if (bk > kKeyFloor) {
       const int col = ir + d0 + (useb ? kHalf : 0) + static_cast<int>(__float_as_uint(bk) & 0xffu);
       atomicMax(&best[ir], tsk_pack(untag_key(bk), col));
     }
     const float2 ck = w.colbuf[lane];
     const int ja = ir + d0;
-    if (ck.x > -2.f && ja < l)
-      atomicMax(&best[ja], tsk_pack(untag_key(ck.x), ir - static_cast<int>(__float_as_uint(ck.x) & 0xffu)));
-    if (ck.y > -2.f && ja + kHalf < l)
-      atomicMax(&best[ja + kHalf], tsk_pack(untag_key(ck.y), ir - static_cast<int>(__float_as_uint(ck.y) & 0xffu)));
+    if (ck.x > kKeyFloor && ja < l)
+      atomicMax(&bestc[ja], tsk_pack(untag_key(ck.x), ir - static_cast<int>(__float_as_uint(ck.x) & 0xffu)));
+    if (ck.y > kKeyFloor && ja + kHalf < l)
+      atomicMax(&bestc[ja + kHalf], tsk_pack(untag_key(ck.y), ir - static_cast<int>(__float_as_uint(ck.y) & 0xffu)));
   }
   __syncwarp();
 }
 
-template <bool MASKED, typename TX>
-__device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ x, int n, int l, int64_t wb, int d0,
-                                        int r0, int rEnd, MpWarpSmem& w, int lane) {
+// Row side: stream x (n samples, window arrays at wb); column side: stream xc
+// (nc samples, lc windows, window arrays at wbc).  The self-join passes the
+// same stream twice (AB = false: the column pointers are the row pointers).
+template <bool MASKED, bool AB, typename TX>
+__device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ x, int64_t wb,
+                                        const TX* __restrict__ xc, int nc, int l, int64_t wbc, int d0, int r0,
+                                        int rEnd, MpWarpSmem& w, int lane) {
   const float* __restrict__ inv = a.wa.inv + wb;
   const float* __restrict__ df = a.wa.df + wb;
   const float* __restrict__ dg = a.wa.dg + wb;
   unsigned long long* __restrict__ best = a.wa.best + wb;
+  const float* __restrict__ invc = AB ? a.wa.inv + wbc : inv;
+  const float* __restrict__ dfc = AB ? a.wa.df + wbc : df;
+  const float* __restrict__ dgc = AB ? a.wa.dg + wbc : dg;
+  unsigned long long* __restrict__ bestc = AB ? a.wa.best + wbc : best;
   const int m = a.m;
   const int dA = d0 + lane * kVh;  // first diagonal of half a (half b: + kHalf)
+  const float2 kMinusOne2 = make_float2(-1.f, -1.f);
 
   // ---- exact anchors c(r0, r0 + dA + v) and c(r0, r0 + dA + 256 + v) in float64:
   //      sum_t (x[r0+t] - mean_r0) * x[c + t]
@@ -320,8 +352,8 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
     for (int v = 0; v < kVh; ++v) {
       accA[v] = 0.0;
       accB[v] = 0.0;
-      wa_[v] = ld_guard(x, baseA + v, n);
-      wbv[v] = ld_guard(x, baseB + v, n);
+      wa_[v] = ld_guard(xc, baseA + v, nc);
+      wbv[v] = ld_guard(xc, baseB + v, nc);
     }
     const double mr = a.wa.mu[wb + r0];
     int t0 = 0;
@@ -334,16 +366,16 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
           accA[v] = fma(at, wa_[(v + u) & (kVh - 1)], accA[v]);
           accB[v] = fma(at, wbv[(v + u) & (kVh - 1)], accB[v]);
         }
-        wa_[u] = ld_guard(x, baseA + t0 + u + kVh, n);
-        wbv[u] = ld_guard(x, baseB + t0 + u + kVh, n);
+        wa_[u] = ld_guard(xc, baseA + t0 + u + kVh, nc);
+        wbv[u] = ld_guard(xc, baseB + t0 + u + kVh, nc);
       }
     }
     for (int t = t0; t < m; ++t) {
       const double at = static_cast<double>(x[r0 + t]) - mr;
 #pragma unroll
       for (int v = 0; v < kVh; ++v) {
-        accA[v] = fma(at, ld_guard(x, baseA + v + t, n), accA[v]);
-        accB[v] = fma(at, ld_guard(x, baseB + v + t, n), accB[v]);
+        accA[v] = fma(at, ld_guard(xc, baseA + v + t, nc), accA[v]);
+        accB[v] = fma(at, ld_guard(xc, baseB + v + t, nc), accB[v]);
       }
     }
 #pragma unroll
@@ -357,9 +389,9 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
 #pragma unroll
   for (int v = 0; v < kVh; ++v) {
     const int j = r0 + dA + v;
-    cdf2[v] = make_float2(df[j], df[j + kHalf]);
-    cdg2[v] = make_float2(dg[j], dg[j + kHalf]);
-    cinv2[v] = make_float2(inv[j], inv[j + kHalf]);
+    cdf2[v] = make_float2(dfc[j], dfc[j + kHalf]);
+    cdg2[v] = make_float2(dgc[j], dgc[j + kHalf]);
+    cinv2[v] = make_float2(invc[j], invc[j + kHalf]);
     ckA[v] = kEmpty;
     ckB[v] = kEmpty;
     tagv[v] = static_cast<unsigned>(lane * kVh + v);
@@ -376,7 +408,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
   // initial fill: ring entries [8, 8 + kRingInit) and the rows of the first chunk
   for (int e = kVh + lane; e < kVh + kRingInit; e += 32) {
     const int j = colbase + e;
-    ring_store(e, df[j], df[j + kHalf], dg[j], dg[j + kHalf], inv[j], inv[j + kHalf]);
+    ring_store(e, dfc[j], dfc[j + kHalf], dgc[j], dgc[j + kHalf], invc[j], invc[j + kHalf]);
   }
   {
     float2* rr = reinterpret_cast<float2*>(&w.rrow[0][0][0]);
@@ -400,12 +432,12 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
       float* d0p = reinterpret_cast<float*>(&w.ring[0][ring_phys(e % kRingEntries)]);
       float* d1p = reinterpret_cast<float*>(&w.ring[1][ring_phys(e % kRingEntries)]);
       float* d2p = reinterpret_cast<float*>(&w.ring[2][ring_phys(e % kRingEntries)]);
-      cp_async4(d0p, df + j);
-      cp_async4(d0p + 1, df + j + kHalf);
-      cp_async4(d1p, dg + j);
-      cp_async4(d1p + 1, dg + j + kHalf);
-      cp_async4(d2p, inv + j);
-      cp_async4(d2p + 1, inv + j + kHalf);
+      cp_async4(d0p, dfc + j);
+      cp_async4(d0p + 1, dfc + j + kHalf);
+      cp_async4(d1p, dgc + j);
+      cp_async4(d1p + 1, dgc + j + kHalf);
+      cp_async4(d2p, invc + j);
+      cp_async4(d2p + 1, invc + j + kHalf);
       float* rr = reinterpret_cast<float*>(&w.rrow[buf ^ 1][0][0]);
       const int i = r0 + S0 + kChunk + lane;
       cp_async4(rr + 2 * lane, df + i);
@@ -442,7 +474,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
         for (int v = 0; v < kVh; ++v) {
           const int c = (v + sr) & (kVh - 1);
           const float2 t = __fmul2_rn(cov2[v], cinv2[c]);
-          const float2 r = __fmul2_rn(t, rinv2);
+          const float2 r = __ffma2_rn(t, rinv2, kMinusOne2);  // rho - 1: full relative precision near rho = 1
           float ka = tag_key(r.x, tagv[v]);
           float kb = tag_key(r.y, tagv[v]);
           if (MASKED) {
@@ -477,7 +509,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
       }
     }
     }
-    flush_chunk(w, kChunk, r0 + S0, d0, l, best, lane);
+    flush_chunk(w, kChunk, r0 + S0, d0, l, best, bestc, lane);
   }
   cp_async_wait_all();
   __syncwarp();
@@ -486,14 +518,14 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
   for (int v = 0; v < kVh; ++v) {
     const int j = r0 + nsteps + dA + v;
     const int row0 = r0 + nsteps + lane * kVh + v;  // = j - d0
-    if (ckA[v] > -2.f && j < l)
-      atomicMax(&best[j], tsk_pack(untag_key(ckA[v]), row0 - static_cast<int>(__float_as_uint(ckA[v]) & 0xffu)));
-    if (ckB[v] > -2.f && j + kHalf < l)
-      atomicMax(&best[j + kHalf], tsk_pack(untag_key(ckB[v]), row0 - static_cast<int>(__float_as_uint(ckB[v]) & 0xffu)));
+    if (ckA[v] > kKeyFloor && j < l)
+      atomicMax(&bestc[j], tsk_pack(untag_key(ckA[v]), row0 - static_cast<int>(__float_as_uint(ckA[v]) & 0xffu)));
+    if (ckB[v] > kKeyFloor && j + kHalf < l)
+      atomicMax(&bestc[j + kHalf], tsk_pack(untag_key(ckB[v]), row0 - static_cast<int>(__float_as_uint(ckB[v]) & 0xffu)));
   }
 }
 
-template <typename TX>
+template <typename TX, bool AB>
 __global__ void __launch_bounds__(kWarps * 32, 3) k_mp_diag(MpArgs a) {
   extern __shared__ __align__(16) unsigned char mp_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -529,14 +561,31 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_mp_diag(MpArgs a) {
           ++wk;
         }
       }
-      const int n = a.len[q];
-      const int l = n - a.m + 1;
-      const TX* x = static_cast<const TX*>(a.X) + a.xoff[q];
-      const int64_t wb = a.woff[q];
+      const TX* X = static_cast<const TX*>(a.X);
+      const TX* x;
+      const TX* xc;
+      int nc;
+      int64_t wb, wbc;
+      if (AB) {
+        const TX* X2 = static_cast<const TX*>(a.X2);
+        const int p = q < a.split ? q + a.split : q - a.split;  // the partner stream
+        x = stream_base(X, X2, a.xoff, a.split, q);
+        xc = stream_base(X, X2, a.xoff, a.split, p);
+        nc = a.len[p];
+        wb = a.woff[q];
+        wbc = a.woff[p];
+      } else {
+        x = X + a.xoff[q];
+        xc = x;
+        nc = a.len[q];
+        wb = a.woff[q];
+        wbc = wb;
+      }
+      const int lc = nc - a.m + 1;
       if (!masked)
-        mp_tile<false, TX>(a, x, n, l, wb, d0, r0, rEnd, w, lane);
+        mp_tile<false, AB, TX>(a, x, wb, xc, nc, lc, wbc, d0, r0, rEnd, w, lane);
       else
-        mp_tile<true, TX>(a, x, n, l, wb, d0, r0, rEnd, w, lane);
+        mp_tile<true, AB, TX>(a, x, wb, xc, nc, lc, wbc, d0, r0, rEnd, w, lane);
     }
   }
 }
@@ -593,64 +642,82 @@ __global__ void __launch_bounds__(128) k_mp_diag_f64(MpArgs a, int pass) {
 // ---------------------------------------------------------------------------
 // 4. refinement: exact distance to each window's chosen neighbour
 // ---------------------------------------------------------------------------
-template <typename TX, typename TP>
-__global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, const int64_t* __restrict__ xoff,
+template <typename TX, typename TP, bool AB>
+__global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, const TX* __restrict__ X2, int split,
+                                                   const int64_t* __restrict__ xoff,
                                                    const int32_t* __restrict__ len, const uint8_t* __restrict__ smask,
                                                    const int64_t* __restrict__ woff, int n_streams, int64_t total, int m,
                                                    int excl, int exact64, WinArrays wa, TP* __restrict__ P,
-                                                   int32_t* __restrict__ I) {
+                                                   int32_t* __restrict__ I, TP* __restrict__ P2,
+                                                   int32_t* __restrict__ I2) {
   const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= total) return;
   const int q = tsk_find_segment<int64_t>(xoff, n_streams, e);
   if (!smask[q]) return;
+  // output slot: the AB join writes the training side's profile to P2 / I2
+  TP* Pout = P;
+  int32_t* Iout = I;
+  int64_t eo = e;
+  if (AB && q >= split) {
+    if (!P2) return;
+    Pout = P2;
+    Iout = I2;
+    eo = e - xoff[split];
+  }
   const int n = len[q];
   const int l = n - m + 1;
   const int i = static_cast<int>(e - xoff[q]);
   if (i >= l) {
-    P[e] = static_cast<TP>(NAN);
-    I[e] = -1;
+    Pout[eo] = static_cast<TP>(NAN);
+    Iout[eo] = -1;
     return;
   }
-  const int64_t wb = woff[q];
-  const TX* x = X + xoff[q];
+  const int p = AB ? (q < split ? q + split : q - split) : q;  // stream holding the candidates
+  const int lp = len[p] - m + 1;
+  const int64_t wb = woff[q], wbp = woff[p];
+  const TX* x = AB ? stream_base(X, X2, xoff, split, q) : X + xoff[q];
+  const TX* xp = AB ? stream_base(X, X2, xoff, split, p) : x;
   // lowest admissible constant window
   int jc = -1;
-  if (wa.constcnt[q] > 0) {
-    const int f = wa.nxt[wb];
-    if (f <= i - excl) jc = f;
-    else if (i + excl < l) {
+  if (wa.constcnt[p] > 0) {
+    const int f = wa.nxt[wbp];
+    if (AB) {
+      if (f < lp) jc = f;
+    } else if (f <= i - excl) {
+      jc = f;
+    } else if (i + excl < l) {
       const int g = wa.nxt[wb + i + excl];
       if (g < l) jc = g;
     }
   }
   const double sqm = sqrt(static_cast<double>(m));
   if (wa.inv[wb + i] == 0.f) {
-    if (jc >= 0) { P[e] = static_cast<TP>(0); I[e] = jc; return; }
-    const int jl = (i >= excl) ? 0 : ((i + excl < l) ? i + excl : -1);
-    P[e] = static_cast<TP>(jl >= 0 ? sqm : INFINITY);
-    I[e] = jl;
+    if (jc >= 0) { Pout[eo] = static_cast<TP>(0); Iout[eo] = jc; return; }
+    const int jl = AB ? 0 : ((i >= excl) ? 0 : ((i + excl < l) ? i + excl : -1));
+    Pout[eo] = static_cast<TP>(jl >= 0 ? sqm : INFINITY);
+    Iout[eo] = jl;
     return;
   }
   int j = -1;
   if (exact64) {
     const int b = wa.bidx[wb + i];  // initialised to 0x7f7f7f7f (no neighbour)
-    j = (b >= l) ? -1 : b;
+    j = (b >= lp) ? -1 : b;
   } else {
     const unsigned long long pk = wa.best[wb + i];
     j = pk ? tsk_unpack_idx(pk) : -1;
   }
   double dist = INFINITY;
   if (j >= 0) {
-    if (wa.inv[wb + j] == 0.f) {
+    if (wa.inv[wbp + j] == 0.f) {
       dist = sqm;
     } else {
-      const double rho = tsk::window_rho(x, i, j, m, wa.mu[wb + i], wa.mu[wb + j]);
+      const double rho = tsk::window_rho(x, i, xp, j, m, wa.mu[wb + i], wa.mu[wbp + j]);
       dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - rho)));
     }
   }
   if (jc >= 0 && (sqm < dist || (sqm == dist && jc < j))) { dist = sqm; j = jc; }
-  P[e] = static_cast<TP>(dist);
-  I[e] = j;
+  Pout[eo] = static_cast<TP>(dist);
+  Iout[eo] = j;
 }
 
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel), and
@@ -680,8 +747,9 @@ cudaError_t set_smem_limit(K kernel, int device, int bytes, int /*slot*/) {
 }
 
 template <typename TX>
-tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_plan& plan, int32_t m, int32_t excl,
-                     int32_t precision, void* P, int32_t* I, char* ws) {
+tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, bool ab, int32_t n_streams,
+                     const tsk_mp_plan& plan, int32_t m, int32_t excl, int32_t precision, void* P, int32_t* I,
+                     void* P2, int32_t* I2, char* ws) {
   tsk_carver cv(ws);
   const int64_t W = plan.total_windows;
   const bool f64 = precision == TSK_MP_FP64;
@@ -708,13 +776,15 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
     const size_t smem = sizeof(double) * 2 * (kWinChunk + m + 2);
     TSK_CUDA_TRY(ctx, set_smem_limit(k_window_stats<TX>, ctx->device, static_cast<int>(smem), 0));
     k_window_stats<TX><<<static_cast<unsigned>(plan.total_chunks), kWinThreads, smem, st>>>(
-        X, plan.xoff, plan.len, plan.woff, plan.chunk_prefix, n_streams, m, f64 ? 1 : 0, wa, ctx->d_err);
+        X, X2, split, plan.xoff, plan.len, plan.woff, plan.chunk_prefix, n_streams, m, f64 ? 1 : 0, wa, ctx->d_err);
     TSK_LAUNCH_CHECK(ctx, "k_window_stats");
     k_next_const<<<n_streams, kWinThreads, 0, st>>>(plan.len, plan.smask, plan.woff, m, wa);
     TSK_LAUNCH_CHECK(ctx, "k_next_const");
   }
   MpArgs a{};
   a.X = X;
+  a.X2 = X2;
+  a.split = split;
   a.xoff = plan.xoff;
   a.len = plan.len;
   a.woff = plan.woff;
@@ -736,16 +806,17 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
       }
     } else {
       const size_t smem = sizeof(MpWarpSmem) * kWarps;
-      TSK_CUDA_TRY(ctx, set_smem_limit(k_mp_diag<TX>, ctx->device, static_cast<int>(smem), 1));
+      auto kern = ab ? k_mp_diag<TX, true> : k_mp_diag<TX, false>;
+      TSK_CUDA_TRY(ctx, set_smem_limit(kern, ctx->device, static_cast<int>(smem), 1));
       int per_sm = 0;
-      TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<TX>, kWarps * 32, smem));
+      TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem));
       per_sm = std::max(per_sm, 1);
       const int64_t want = (plan.total_tiles + kWarps - 1) / kWarps;
       const int64_t grid = std::min<int64_t>(want, static_cast<int64_t>(per_sm) * ctx->sm_count);
       a.total_warps = static_cast<int>(grid) * kWarps;
       {
         tsk_prof_scope ps(ctx, TSK_PROF_MP_DIAG);
-        k_mp_diag<TX><<<static_cast<unsigned>(grid), kWarps * 32, smem, st>>>(a);
+        kern<<<static_cast<unsigned>(grid), kWarps * 32, smem, st>>>(a);
       }
       TSK_LAUNCH_CHECK(ctx, "k_mp_diag");
     }
@@ -753,10 +824,19 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, int32_t n_streams, const tsk_mp_
   const int64_t total = plan.total_samples;
   if (total > 0) {
     const int64_t blocks = (total + 255) / 256;
+    const unsigned g = static_cast<unsigned>(blocks);
     if (f64)
-      k_mp_refine<TX, double><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, plan.xoff, plan.len, plan.smask, plan.woff, n_streams, total, m, excl, 1, wa, static_cast<double*>(P), I);
+      k_mp_refine<TX, double, false><<<g, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.smask, plan.woff,
+                                                        n_streams, total, m, excl, 1, wa, static_cast<double*>(P), I,
+                                                        nullptr, nullptr);
+    else if (ab)
+      k_mp_refine<TX, float, true><<<g, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.smask, plan.woff,
+                                                      n_streams, total, m, 0, 0, wa, static_cast<float*>(P), I,
+                                                      static_cast<float*>(P2), I2);
     else
-      k_mp_refine<TX, float><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, plan.xoff, plan.len, plan.smask, plan.woff, n_streams, total, m, excl, 0, wa, static_cast<float*>(P), I);
+      k_mp_refine<TX, float, false><<<g, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.smask, plan.woff,
+                                                       n_streams, total, m, excl, 0, wa, static_cast<float*>(P), I,
+                                                       nullptr, nullptr);
     TSK_LAUNCH_CHECK(ctx, "k_mp_refine");
   }
   return TSK_OK;
@@ -781,8 +861,20 @@ size_t tsk_mp_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams) {
 tsk_status tsk_run_mp(tsk_ctx* ctx, const void* X, int x_dtype, int32_t n_streams, const tsk_mp_plan& plan, int32_t m,
                       int32_t excl, int32_t precision, void* P, int32_t* I, char* ws) {
   if (x_dtype == TSK_F64)
-    return run_typed<double>(ctx, static_cast<const double*>(X), n_streams, plan, m, excl, precision, P, I, ws);
-  return run_typed<float>(ctx, static_cast<const float*>(X), n_streams, plan, m, excl, precision, P, I, ws);
+    return run_typed<double>(ctx, static_cast<const double*>(X), static_cast<const double*>(X), n_streams, false,
+                             n_streams, plan, m, excl, precision, P, I, nullptr, nullptr, ws);
+  return run_typed<float>(ctx, static_cast<const float*>(X), static_cast<const float*>(X), n_streams, false, n_streams,
+                          plan, m, excl, precision, P, I, nullptr, nullptr, ws);
+}
+
+tsk_status tsk_run_mp_ab(tsk_ctx* ctx, const void* A, const void* B, int x_dtype, int32_t n_pairs,
+                         const tsk_mp_plan& plan, int32_t m, void* P_a, int32_t* I_a, void* P_b, int32_t* I_b,
+                         char* ws) {
+  if (x_dtype == TSK_F64)
+    return run_typed<double>(ctx, static_cast<const double*>(A), static_cast<const double*>(B), n_pairs, true,
+                             2 * n_pairs, plan, m, 0, TSK_MP_FP32, P_a, I_a, P_b, I_b, ws);
+  return run_typed<float>(ctx, static_cast<const float*>(A), static_cast<const float*>(B), n_pairs, true, 2 * n_pairs,
+                          plan, m, 0, TSK_MP_FP32, P_a, I_a, P_b, I_b, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -817,7 +909,7 @@ tsk_status static_setup(int dev, void** out) {
     const int win_smem = static_cast<int>(sizeof(double) * 2 * (kWinChunk + 4096 + 2));
     if (cudaFuncSetAttribute(k_window_stats<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, win_smem) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(k_mp_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_mp_diag<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sizeof(MpWarpSmem) * kWarps)) != cudaSuccess) {
       cudaGetLastError();
       return TSK_ERR_CUDA;
@@ -913,11 +1005,13 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
 
   const size_t win_smem = sizeof(double) * 2 * (kWinChunk + m + 2);
   k_window_stats<float><<<static_cast<unsigned>(h.chunk_prefix[1]), kWinThreads, win_smem, stream>>>(
-      X, dh->xoff, dh->len, dh->woff, dh->chunk_prefix, 1, m, 0, wa, err);
+      X, X, 1, dh->xoff, dh->len, dh->woff, dh->chunk_prefix, 1, m, 0, wa, err);
   k_next_const<<<1, kWinThreads, 0, stream>>>(dh->len, dh->smask, dh->woff, m, wa);
   if (!tiles.empty()) {
     MpArgs a{};
     a.X = X;
+    a.X2 = X;
+    a.split = 1;
     a.xoff = dh->xoff;
     a.len = dh->len;
     a.woff = dh->woff;
@@ -931,17 +1025,17 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
     a.H = H;
     const size_t smem = sizeof(MpWarpSmem) * kWarps;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<float>, kWarps * 32, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<float, false>, kWarps * 32, smem) != cudaSuccess) {
       cudaGetLastError();
       return TSK_ERR_CUDA;
     }
     per_sm = std::max(per_sm, 1);
     const int64_t grid = std::min<int64_t>((a.total_tiles + kWarps - 1) / kWarps, static_cast<int64_t>(per_sm) * sms);
     a.total_warps = static_cast<int>(grid) * kWarps;
-    k_mp_diag<float><<<static_cast<unsigned>(grid), kWarps * 32, smem, stream>>>(a);
+    k_mp_diag<float, false><<<static_cast<unsigned>(grid), kWarps * 32, smem, stream>>>(a);
   }
-  k_mp_refine<float, float><<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
-      X, dh->xoff, dh->len, dh->smask, dh->woff, 1, n, m, excl, 0, wa, P, I);
+  k_mp_refine<float, float, false><<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
+      X, X, 1, dh->xoff, dh->len, dh->smask, dh->woff, 1, n, m, excl, 0, wa, P, I, nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return TSK_ERR_CUDA;
   return TSK_OK;
 }

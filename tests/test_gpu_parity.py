@@ -316,3 +316,19 @@ def test_backward_matches_oracle_adjoint(tsk):
     scale_T = np.abs(dT).max()
     np.testing.assert_allclose(gT, dT, rtol=0, atol=1e-3 * scale_T)
     np.testing.assert_allclose(gR, dR, rtol=1e-3, atol=1e-3 * np.abs(dR).max())
+
+
+def test_close_matches_meet_the_tolerance(tsk):
+    """Noisy periodic streams: every window has near-repeats (1 - rho ~ 1e-3), where float32
+    keys must still tell neighbours apart to 1e-3 relative in the distance."""
+    rng = np.random.default_rng(61)
+    m, excl = 40, 10
+    xs = []
+    for n, noise in ((6000, 0.02), (3000, 0.05), (4500, 0.01)):
+        t = np.arange(n)
+        xs.append((np.sin(2 * np.pi * t / 50) + 0.5 * np.sin(2 * np.pi * t / 17) + noise * rng.normal(size=n))
+                  .astype(np.float32))
+    out = _streams(tsk, xs, m, excl)
+    for x, (P, I) in zip(xs, out):
+        l = len(x) - m + 1
+        check_profile(x.astype(np.float64), m, excl, P[:l], I[:l], rows=np.arange(0, l, 3))
