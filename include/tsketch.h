@@ -181,6 +181,30 @@ TSK_API tsk_status mp_selfjoin(tsk_ctx* ctx, const void* X, int32_t x_dtype, int
                                int32_t excl, int32_t precision, void* P, int32_t* I);
 
 /*
+ * mp_abjoin - AB-join matrix profile (Def. 6 with T_test != T_train), the
+ * form Alg. 2 runs on: for every window i of test stream A_q,
+ *   P_a[i] = min over EVERY window j of training stream B_q of dist(A_q[i:i+m], B_q[j:j+m]),
+ *   I_a[i] = that j (a tie may return any j at the same distance),
+ * and, optionally, the training side's profile against the test stream
+ * (P_b, I_b: for every window of B_q its nearest window of A_q).  No
+ * exclusion zone; the constant-window rules of mp_selfjoin apply.
+ *   A, B        : device streams, packed like mp_selfjoin's X (A: n_pairs
+ *                 streams of len_a_host[q] samples; B: n_pairs streams of
+ *                 len_b_host[q]); both float32 or both float64 (x_dtype).
+ *   P_a, I_a    : device float32 / int32, packed like A (entries past the
+ *                 last window are NaN / -1).
+ *   P_b, I_b    : optional (both NULL to skip), packed like B.
+ *   precision   : TSK_MP_FP32 (the float32 recurrence with float64 anchors and
+ *                 an exact re-evaluation of each chosen neighbour);
+ *                 TSK_MP_FP64 returns TSK_ERR_UNSUPPORTED.
+ * Errors: TSK_ERR_INVALID_ARG for NULL required arrays, only one of P_b / I_b,
+ * a bad dtype, m outside [2, 4096] or a stream shorter than m.
+ */
+TSK_API tsk_status mp_abjoin(tsk_ctx* ctx, const void* A, const void* B, int32_t x_dtype, int32_t n_pairs,
+                             const int32_t* len_a_host, const int32_t* len_b_host, int32_t m, int32_t precision,
+                             void* P_a, int32_t* I_a, void* P_b, int32_t* I_b);
+
+/*
  * discord_topk - aggregate over the streams of each series and rank the
  * discords (Def. 5, Alg. 2 extended to a ranked list of K).
  *

@@ -5,6 +5,7 @@ include/tsketch.h; this package is its thin Python binding plus seeded
 synthetic workloads (synth).
 """
 from .api import (  # noqa: F401
+    ab_discords,
     DiscordScores,
     context,
     default_excl,
@@ -12,6 +13,7 @@ from .api import (  # noqa: F401
     discord_topk,
     exact_discords,
     launch_count,
+    mp_abjoin,
     mp_backward,
     mp_selfjoin,
     pack_batch,

@@ -148,6 +148,55 @@ def mp_selfjoin(X: torch.Tensor, stream_len: Sequence[int], m: int, excl: int | 
     return P, I
 
 
+def mp_abjoin(A: torch.Tensor, B: torch.Tensor, len_a: Sequence[int], len_b: Sequence[int], m: int,
+              train_profile: bool = False):
+    """AB-join profiles (Def. 6): each test window of A_q against every window of B_q.
+
+    Returns (P_a, I_a) packed like A, plus (P_b, I_b) packed like B when
+    train_profile (each training window's nearest test window).
+    """
+    _need_cuda(A, B)
+    if A.dtype != B.dtype:
+        raise ValueError("A and B must share a dtype")
+    n = len(len_a)
+    if len(len_b) != n:
+        raise ValueError("len_a and len_b must have one entry per stream pair")
+    dev = A.device
+    P_a = torch.empty(A.numel(), dtype=torch.float32, device=dev)
+    I_a = torch.empty(A.numel(), dtype=torch.int32, device=dev)
+    P_b = torch.empty(B.numel(), dtype=torch.float32, device=dev) if train_profile else None
+    I_b = torch.empty(B.numel(), dtype=torch.int32, device=dev) if train_profile else None
+    la, lap = _i32_array(len_a)
+    lb, lbp = _i32_array(len_b)
+    h = _ctx(dev)
+    N.check(N.lib().mp_abjoin(h, _ptr(A), _ptr(B), _dtype_code(A), n, lap, lbp, int(m), MP_PRECISION["fp32"],
+                              _ptr(P_a), _ptr(I_a), _ptr(P_b) if train_profile else None,
+                              _ptr(I_b) if train_profile else None), h, "mp_abjoin")
+    return (P_a, I_a, P_b, I_b) if train_profile else (P_a, I_a)
+
+
+def ab_discords(T_test: torch.Tensor, T_train: torch.Tensor, test_len: Sequence[int], train_len: Sequence[int],
+                d: int, m: int, K: int, R: torch.Tensor | None = None, topk_excl: int | None = None,
+                sketch_precision: str = "bf16"):
+    """Discords of test series against training series (Def. 5 in train/test form, Alg. 2).
+
+    With R both are z-normalised over their own length and sketched with R,
+    and the k sketch streams are AB-joined; without R the d raw streams are.
+    """
+    if R is not None:
+        k = int(R.shape[1])
+        A, sa = ts_sketch_build(T_test, R, test_len, d, precision=sketch_precision)
+        B, sb = ts_sketch_build(T_train, R, train_len, d, precision=sketch_precision)
+        g = k
+    else:
+        A, B, sa, sb, g = T_test, T_train, None, None, d
+    la = [n for n in test_len for _ in range(g)]
+    lb = [n for n in train_len for _ in range(g)]
+    P, I = mp_abjoin(A, B, la, lb, m)
+    idx, grp, score, nn = discord_topk(P, I, test_len, g, m, K, topk_excl)
+    return {"S_test": A, "S_train": B, "P": P, "I": I, "idx": idx, "grp": grp, "score": score, "nn": nn}
+
+
 def discord_topk(P: torch.Tensor, I: torch.Tensor, series_len: Sequence[int], group: int, m: int, K: int,
                  topk_excl: int | None = None):
     """Aggregate over each series' `group` streams and rank K discords (Def. 5, Alg. 2).

@@ -161,24 +161,50 @@ tsk_status batch_layout(tsk_ctx* ctx, int32_t n_series, const int32_t* lens, int
   return TSK_OK;
 }
 
+// Work units of one row stream against one column stream (the same stream for
+// a self-join) on diagonals dmin, dmin+1, ...: bands of D diagonals, rows cut
+// into units of H; rows where every diagonal of the band is valid go to
+// `interior`, the band's last rows (diagonals running out, or the row side
+// ending) to `tail` as one masked unit.
+void add_units(int32_t q, int64_t l_row, int64_t l_col, int64_t dmin, int32_t H, int32_t D, int32_t chunk_rows,
+               std::vector<int32_t>& interior, std::vector<int32_t>& tail) {
+  for (int64_t d0 = dmin; d0 < l_col; d0 += D) {
+    const int64_t rows = std::min(l_row, l_col - d0);                                 // rows with a cell
+    int64_t rint = std::min(l_row, std::max<int64_t>(0, l_col - d0 - (D - 1)));       // rows with all D
+    rint -= rint % chunk_rows;
+    for (int64_t r0 = 0; r0 < rint; r0 += H) {
+      const int64_t r1 = std::min<int64_t>(r0 + H, rint);
+      interior.insert(interior.end(), {q, static_cast<int32_t>(d0), static_cast<int32_t>(r0), static_cast<int32_t>(r1)});
+    }
+    if (rows > rint)
+      tail.insert(tail.end(), {q, static_cast<int32_t>(d0), static_cast<int32_t>(rint),
+                               static_cast<int32_t>(static_cast<uint32_t>(rows) | 0x80000000u)});
+  }
+}
+
+int32_t auto_rows(tsk_ctx* ctx, double cells) {
+  // rows per work unit: about 64 units per resident warp, within [2048, 8192]
+  // (warps claim runs of consecutive units, so small units cost few anchors)
+  const int32_t D = tsk_mp_band_width();
+  const double warps = static_cast<double>(ctx->sm_count) * 12.0;
+  const double rows = cells / (warps * 64.0 * D);
+  const int32_t step = tsk_mp_chunk_rows();
+  int32_t H = static_cast<int32_t>(std::min(8192.0, std::max(2048.0, rows)));
+  return (H + step - 1) / step * step;
+}
+
 tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* mask, int32_t m, int32_t excl,
                    int32_t prec, tsk_mp_plan* plan) {
   const int32_t D = tsk_mp_band_width();
   int32_t H = ctx->mp_H;
   if (H <= 0) {
-    // rows per work unit: about 64 units per resident warp, within [2048, 8192]
-    // (warps claim runs of consecutive units, so small units cost few anchors)
     double cells = 0.0;
     for (int q = 0; q < n; ++q) {
       if (mask && !mask[q]) continue;
       const double e = static_cast<double>(lens[q]) - m + 1 - excl;
       if (e > 0) cells += e * (e + 1) / 2;
     }
-    const double warps = static_cast<double>(ctx->sm_count) * 12.0;
-    const double rows = cells / (warps * 64.0 * D);
-    const int32_t step = tsk_mp_chunk_rows();
-    H = static_cast<int32_t>(std::min(8192.0, std::max(2048.0, rows)));
-    H = (H + step - 1) / step * step;
+    H = auto_rows(ctx, cells);
   }
   std::string key = "mp";
   const int32_t hdr[6] = {n, m, excl, prec, H, D};
@@ -206,19 +232,7 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
       chp[q + 1] = chp[q] + (on ? (l + chunk - 1) / chunk : 0);
       tp[q + 1] = tp[q] + ((on && prec == TSK_MP_FP64) ? std::max<int64_t>(0, l - excl) : 0);
       if (!on || prec == TSK_MP_FP64 || l <= excl) continue;
-      for (int64_t d0 = excl; d0 < l; d0 += D) {
-        const int64_t rows = l - d0;                       // rows with at least one cell
-        int64_t rint = std::max<int64_t>(0, rows - (D - 1));  // rows with all D diagonals
-        rint -= rint % chunk_rows;
-        for (int64_t r0 = 0; r0 < rint; r0 += H) {
-          const int64_t r1 = std::min<int64_t>(r0 + H, rint);
-          tiles_int.insert(tiles_int.end(), {q, static_cast<int32_t>(d0), static_cast<int32_t>(r0),
-                                             static_cast<int32_t>(r1)});
-        }
-        if (rows > rint)
-          tiles_tri.insert(tiles_tri.end(), {q, static_cast<int32_t>(d0), static_cast<int32_t>(rint),
-                                             static_cast<int32_t>(static_cast<uint32_t>(rows) | 0x80000000u)});
-      }
+      add_units(q, l, l, excl, H, D, chunk_rows, tiles_int, tiles_tri);
     }
     tiles_int.insert(tiles_int.end(), tiles_tri.begin(), tiles_tri.end());
     const int64_t ntiles = prec == TSK_MP_FP64 ? tp[n] : static_cast<int64_t>(tiles_int.size() / 4);
@@ -245,6 +259,85 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
   plan->H = H;
   plan->D = D;
   plan->prec = prec;
+  plan->total_windows = b->meta[0];
+  plan->total_chunks = b->meta[1];
+  plan->total_tiles = b->meta[2];
+  plan->total_samples = b->meta[3];
+  plan->xoff = reinterpret_cast<int64_t*>(base + b->meta[4]);
+  plan->len = reinterpret_cast<int32_t*>(base + b->meta[5]);
+  plan->smask = reinterpret_cast<uint8_t*>(base + b->meta[6]);
+  plan->woff = reinterpret_cast<int64_t*>(base + b->meta[7]);
+  plan->chunk_prefix = reinterpret_cast<int64_t*>(base + b->meta[8]);
+  plan->tile_prefix = reinterpret_cast<int64_t*>(base + b->meta[9]);
+  plan->tiles = reinterpret_cast<int4*>(base + b->meta[10]);
+  return TSK_OK;
+}
+
+// AB join: streams 0..n-1 are the test streams, n..2n-1 their training
+// partners.  Test rows against training columns on diagonals >= 0, then
+// training rows against test columns on diagonals >= 1.
+tsk_status mp_plan_ab(tsk_ctx* ctx, int32_t n, const int32_t* len_a, const int32_t* len_b, int32_t m,
+                      tsk_mp_plan* plan) {
+  const int32_t D = tsk_mp_band_width();
+  int32_t H = ctx->mp_H;
+  if (H <= 0) {
+    double cells = 0.0;
+    for (int q = 0; q < n; ++q) cells += static_cast<double>(len_a[q] - m + 1) * static_cast<double>(len_b[q] - m + 1);
+    H = auto_rows(ctx, cells);
+  }
+  std::string key = "mpab";
+  const int32_t hdr[4] = {n, m, H, D};
+  append(key, hdr, 4);
+  append(key, len_a, n);
+  append(key, len_b, n);
+  tsk_status st = TSK_OK;
+  const int pad = tsk_mp_pad();
+  const int chunk = tsk_mp_chunk();
+  const Blob* b = blob_get(ctx, key, [&](std::vector<char>& buf, std::vector<int64_t>& meta) {
+    const int N = 2 * n;
+    std::vector<int64_t> xoff(N + 1, 0), woff(N + 1, 0), chp(N + 1, 0), tp(N + 1, 0);
+    std::vector<int32_t> len(N);
+    std::vector<uint8_t> sm(N, 1);
+    for (int q = 0; q < n; ++q) {
+      len[q] = len_a[q];
+      len[n + q] = len_b[q];
+    }
+    std::vector<int32_t> tiles_int, tiles_tri;
+    const int32_t chunk_rows = tsk_mp_chunk_rows();
+    for (int q = 0; q < N; ++q) {
+      const int64_t l = static_cast<int64_t>(len[q]) - m + 1;
+      xoff[q + 1] = xoff[q] + len[q];
+      woff[q + 1] = woff[q] + ((l + pad + 3) & ~int64_t(3));
+      chp[q + 1] = chp[q] + (l + chunk - 1) / chunk;
+    }
+    for (int q = 0; q < N; ++q) {
+      const int p = q < n ? q + n : q - n;
+      add_units(q, static_cast<int64_t>(len[q]) - m + 1, static_cast<int64_t>(len[p]) - m + 1, q < n ? 0 : 1, H, D,
+                chunk_rows, tiles_int, tiles_tri);
+    }
+    tiles_int.insert(tiles_int.end(), tiles_tri.begin(), tiles_tri.end());
+    meta.assign(11, 0);
+    meta[0] = woff[N];
+    meta[1] = chp[N];
+    meta[2] = static_cast<int64_t>(tiles_int.size() / 4);
+    meta[3] = xoff[N];
+    meta[4] = static_cast<int64_t>(put(buf, xoff));
+    meta[5] = static_cast<int64_t>(put(buf, len));
+    meta[6] = static_cast<int64_t>(put(buf, sm));
+    meta[7] = static_cast<int64_t>(put(buf, woff));
+    meta[8] = static_cast<int64_t>(put(buf, chp));
+    meta[9] = static_cast<int64_t>(put(buf, tp));
+    meta[10] = static_cast<int64_t>(put(buf, tiles_int));
+  }, &st);
+  if (!b) return st;
+  if (b->meta[2] > 0x7fffffffLL)
+    return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "mp_abjoin: more than 2^31 work units; raise tsk_set_tile_rows");
+  char* base = static_cast<char*>(b->dev);
+  plan->m = m;
+  plan->excl = 0;
+  plan->H = H;
+  plan->D = D;
+  plan->prec = TSK_MP_FP32;
   plan->total_windows = b->meta[0];
   plan->total_chunks = b->meta[1];
   plan->total_tiles = b->meta[2];
@@ -569,6 +662,27 @@ extern "C" TSK_API tsk_status mp_selfjoin(tsk_ctx* ctx, const void* X, int32_t x
   if ((st = mp_plan(ctx, n_streams, stream_len_host, stream_mask_host, m, excl, precision, &plan))) return st;
   if ((st = tsk_ws_require(ctx, tsk_mp_ws_bytes(plan, n_streams)))) return st;
   return tsk_run_mp(ctx, X, x_dtype, n_streams, plan, m, excl, precision, P, I, static_cast<char*>(ctx->ws));
+}
+
+extern "C" TSK_API tsk_status mp_abjoin(tsk_ctx* ctx, const void* A, const void* B, int32_t x_dtype, int32_t n_pairs,
+                                        const int32_t* len_a_host, const int32_t* len_b_host, int32_t m,
+                                        int32_t precision, void* P_a, int32_t* I_a, void* P_b, int32_t* I_b) {
+  tsk_status st = enter(ctx);
+  if (st) return st;
+  if (!A || !B || !P_a || !I_a) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: A, B, P_a and I_a must be non-NULL");
+  if ((P_b == nullptr) != (I_b == nullptr))
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: P_b and I_b must be both NULL or both non-NULL");
+  if (x_dtype != TSK_F32 && x_dtype != TSK_F64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: bad x_dtype");
+  if (precision != TSK_MP_FP32)
+    return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "mp_abjoin: only TSK_MP_FP32 is implemented for the AB join");
+  if (n_pairs < 1) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: n_pairs must be >= 1");
+  if (m < 2 || m > 4096) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: need 2 <= m <= 4096 (got %d)", m);
+  if ((st = check_lens(ctx, n_pairs, len_a_host, m, "mp_abjoin (test)"))) return st;
+  if ((st = check_lens(ctx, n_pairs, len_b_host, m, "mp_abjoin (train)"))) return st;
+  tsk_mp_plan plan;
+  if ((st = mp_plan_ab(ctx, n_pairs, len_a_host, len_b_host, m, &plan))) return st;
+  if ((st = tsk_ws_require(ctx, tsk_mp_ws_bytes(plan, 2 * n_pairs)))) return st;
+  return tsk_run_mp_ab(ctx, A, B, x_dtype, n_pairs, plan, m, P_a, I_a, P_b, I_b, static_cast<char*>(ctx->ws));
 }
 
 extern "C" TSK_API tsk_status discord_topk(tsk_ctx* ctx, const void* P, int32_t p_dtype, const int32_t* I,

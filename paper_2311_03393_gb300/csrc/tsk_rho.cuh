@@ -6,7 +6,8 @@
 
 namespace tsk {
 
-// Correlation of windows i and j of a float32 series, accurate to ~1e-12.
+// Correlation of window i of series xa and window j of series xb (float32),
+// accurate to ~1e-12.
 // Both windows are centred in float32 with a two-term mean (the centred values
 // carry a rounding of at most ~2^-24 of themselves, an input-sized
 // perturbation), then sum(ab), sum(aa), sum(bb) are accumulated with
@@ -27,13 +28,14 @@ struct DSum {
   __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
 };
 
-__device__ __forceinline__ double window_rho(const float* __restrict__ x, int i, int j, int m, double mi, double mj) {
+__device__ __forceinline__ double window_rho(const float* __restrict__ xa, int i, const float* __restrict__ xb, int j,
+                                             int m, double mi, double mj) {
   const float mih = static_cast<float>(mi), mil = static_cast<float>(mi - static_cast<double>(mih));
   const float mjh = static_cast<float>(mj), mjl = static_cast<float>(mj - static_cast<double>(mjh));
   DSum sab, saa, sbb;
   for (int t = 0; t < m; ++t) {
-    const float a = __fsub_rn(__fsub_rn(x[i + t], mih), mil);
-    const float b = __fsub_rn(__fsub_rn(x[j + t], mjh), mjl);
+    const float a = __fsub_rn(__fsub_rn(xa[i + t], mih), mil);
+    const float b = __fsub_rn(__fsub_rn(xb[j + t], mjh), mjl);
     sab.add_prod(a, b);
     saa.add_prod(a, a);
     sbb.add_prod(b, b);
@@ -41,15 +43,22 @@ __device__ __forceinline__ double window_rho(const float* __restrict__ x, int i,
   return sab.value() / sqrt(saa.value() * sbb.value());
 }
 // float64 series: the same correlation with float64 sums
-__device__ __forceinline__ double window_rho(const double* __restrict__ x, int i, int j, int m, double mi, double mj) {
+__device__ __forceinline__ double window_rho(const double* __restrict__ xa, int i, const double* __restrict__ xb, int j,
+                                             int m, double mi, double mj) {
   double sab = 0.0, saa = 0.0, sbb = 0.0;
   for (int t = 0; t < m; ++t) {
-    const double a = x[i + t] - mi, b = x[j + t] - mj;
+    const double a = xa[i + t] - mi, b = xb[j + t] - mj;
     sab = fma(a, b, sab);
     saa = fma(a, a, saa);
     sbb = fma(b, b, sbb);
   }
   return sab / sqrt(saa * sbb);
+}
+
+// windows i and j of one series
+template <typename TX>
+__device__ __forceinline__ double window_rho(const TX* __restrict__ x, int i, int j, int m, double mi, double mj) {
+  return window_rho(x, i, x, j, m, mi, mj);
 }
 
 }  // namespace tsk
