@@ -1,10 +1,19 @@
 """Shared helpers for the GPU parity tests: tolerances and oracle-side checks.
 
 Tolerances (float32 matrix profile against the float64 oracle):
-  |P_gpu - P_ref| <= 1e-3 * max(P_ref, d_floor),  d_floor = 1e-2 * sqrt(2m)
-The floor covers exact repeats (P_ref = 0), where float32 data still leave a
-residual distance.  Nearest-neighbour indices must match, except where the
-GPU's neighbour is a tie: its oracle distance equals P_ref within the same
+  |P_gpu - P_ref| <= 1e-3 * max(P_ref, d_floor),  d_floor = 1e-2 * sqrt(2m),
+or, where that relative bar is finer than float32 can resolve, the bound the
+float32 recurrence guarantees:
+  P_ref <= P_gpu <= sqrt(P_ref^2 + 4 m DELTA32).
+The float32 path reports the exact distance of the neighbour it chose, and it
+chooses among correlations computed to within DELTA32 = 1.5e-5 (each recurrence
+step rounds the running covariance: sqrt(2 * 16384 steps) * 2^-24 ~ 1.1e-5 over
+the longest walk between float64 anchors), so the chosen neighbour's true rho
+is within 2 DELTA32 of the best and dist^2 = 2m(1 - rho) is within 4m DELTA32
+of the minimum.  The relative bar is the binding one unless P_ref is below
+about 0.04 sqrt(2m) (close matches, 1 - rho < ~1e-3).  The floor covers exact
+repeats (P_ref = 0).  Nearest-neighbour indices must match, except where the
+GPU's neighbour is a tie: its oracle distance equals P_gpu within the same
 tolerance.  The float64 path uses 1e-9 relative.
 """
 import math
@@ -15,6 +24,17 @@ from oracle import tsk_oracle as o
 
 MP_REL_TOL = 1e-3
 FP64_REL_TOL = 1e-9
+DELTA32 = 1.5e-5
+
+
+def within_mp_tol(P_gpu, P_ref, m, rel=MP_REL_TOL, floor=None):
+    """Elementwise: the relative bar, or the float32 resolution bound (see the module docstring)."""
+    P_gpu = np.asarray(P_gpu, dtype=np.float64)
+    P_ref = np.asarray(P_ref, dtype=np.float64)
+    fl = d_floor(m) if floor is None else floor
+    rel_ok = np.abs(P_gpu - P_ref) <= rel * np.maximum(P_ref, fl)
+    f32_ok = (P_gpu >= P_ref * (1 - 1e-6) - 1e-9) & (P_gpu * P_gpu - P_ref * P_ref <= 4 * m * DELTA32)
+    return rel_ok | f32_ok
 
 
 def d_floor(m: int) -> float:
@@ -37,7 +57,9 @@ def check_profile(x, m, excl, P_gpu, I_gpu, rows=None, rel=MP_REL_TOL, floor=Non
     scale = np.maximum(P_ref[ok], fl)
     err = np.abs(Pg[ok] - P_ref[ok]) / scale
     worst = float(err.max()) if err.size else 0.0
-    assert worst <= rel, f"max rel error {worst:.3g} > {rel} at row {rows[ok][int(np.argmax(err))]}"
+    good = within_mp_tol(Pg[ok], P_ref[ok], m, rel, fl)
+    assert good.all(), (f"max rel error {worst:.3g} > {rel} outside the float32 bound at row "
+                        f"{rows[ok][int(np.argmin(good))]}")
     # indices: equal, or a tie at the same distance
     diff = np.where(ok & (Ig != I_ref))[0]
     Z, _, _, _ = o.znorm_windows(x, m)
@@ -45,7 +67,8 @@ def check_profile(x, m, excl, P_gpu, I_gpu, rows=None, rel=MP_REL_TOL, floor=Non
         i, j = int(rows[r]), int(Ig[r])
         assert j >= 0 and abs(i - j) >= excl, (i, j)
         dij = float(np.sqrt(((Z[i] - Z[j]) ** 2).sum()))
-        assert abs(dij - P_ref[r]) <= rel * max(P_ref[r], fl), (i, j, dij, P_ref[r])
+        assert within_mp_tol(dij, P_ref[r], m, rel, fl) and abs(dij - Pg[r]) <= 1e-4 * max(dij, fl), \
+            (i, j, dij, P_ref[r])
     return worst
 
 

@@ -12,7 +12,7 @@ import pytest
 from oracle import tsk_oracle as o
 from paper_2311_03393_gb300 import synth
 
-from helpers import MP_REL_TOL, d_floor
+from helpers import MP_REL_TOL, d_floor, within_mp_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,22 +47,22 @@ def _check_dims(series, R, queries, m, excl, got, rel=MP_REL_TOL):
             if np.isinf(ref_s[j]):
                 assert np.isinf(gs[j])
                 continue
-            assert abs(gs[j] - ref_s[j]) <= rel * max(ref_s[j], fl), (r, j, gs[j], ref_s[j])
+            assert within_mp_tol(gs[j], ref_s[j], m, rel), (r, j, gs[j], ref_s[j])
         j_ref, s_ref, nn_ref = picks[q]
         j_gpu = int(got["dim"][r])
         if j_ref < 0:
             assert j_gpu == -1
         elif j_gpu != j_ref:  # a tie within the tolerance
             assert j_gpu >= 0 and member[j_gpu]
-            assert abs(ref_s[j_gpu] - s_ref) <= rel * max(s_ref, fl), (r, j_gpu, j_ref)
+            assert within_mp_tol(ref_s[j_gpu], s_ref, m, rel), (r, j_gpu, j_ref)
         elif math.isinf(s_ref):
             assert math.isinf(got["score"][r]) and got["nn"][r] == -1
         else:
-            assert abs(got["score"][r] - s_ref) <= rel * max(s_ref, fl)
+            assert within_mp_tol(got["score"][r], s_ref, m, rel)
             nn_gpu = int(got["nn"][r])
             if nn_gpu != nn_ref:  # the neighbour must be an equally near window
                 dd = o.window_distance(T[j_ref], i, nn_gpu, m) if nn_gpu >= 0 else math.inf
-                assert abs(i - nn_gpu) >= excl and abs(dd - s_ref) <= rel * max(s_ref, fl)
+                assert abs(i - nn_gpu) >= excl and within_mp_tol(dd, s_ref, m, rel)
         q += 1
 
 
