@@ -276,16 +276,28 @@ TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, const int32_t*
  *                T_j* for discord r (zeros when j* = -1), for the optional
  *                refinement (mp_selfjoin over T_sel, then discord_topk with
  *                group 1).
+ *   T_train, train_len_host : optional (NULL for the self-join form): the
+ *                training series in the same batch layout (d streams per
+ *                series, lengths train_len_host[s]).  Then T holds the test
+ *                series, s_j = min over EVERY window t of training stream j of
+ *                dist(T_j[i*:i*+m], T_train_j[t:t+m]) (Def. 6 AB form, Alg. 3
+ *                as printed), excl is ignored, and dim_nn indexes the
+ *                training stream.
+ *   T_sel_train: optional (needs T_train): the chosen training streams, laid
+ *                out like T_sel with the training lengths, for the AB-join
+ *                refinement (mp_abjoin of T_sel against T_sel_train).
  * Errors: TSK_ERR_INVALID_ARG for NULL required arrays, a bad dtype,
- * m outside [2, 4096], excl < 1, K < 1, k < 1, d < 1 or a series shorter than
- * m; nothing is issued then.  Out-of-range idx/grp entries are treated as
- * empty slots.
+ * m outside [2, 4096], excl < 1 (self-join form), K < 1, k < 1, d < 1, a series
+ * shorter than m, T_train without train_len_host, or T_sel_train without
+ * T_train; nothing is issued then.  Out-of-range idx/grp entries are treated
+ * as empty slots.
  */
 TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, int32_t t_dtype, int32_t n_series,
                                        const int32_t* series_len_host, int32_t d, const float* R, int32_t k,
                                        int32_t m, int32_t excl, int32_t K, const int32_t* idx, const int32_t* grp,
                                        int32_t* dim, double* dim_score, int32_t* dim_nn, double* dim_scores,
-                                       void* T_sel);
+                                       void* T_sel, const void* T_train, const int32_t* train_len_host,
+                                       void* T_sel_train);
 
 /*
  * mp_selfjoin_static - the matrix profile of ONE float32 stream, like

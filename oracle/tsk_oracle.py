@@ -413,9 +413,13 @@ def dimension_detection(T, R, discords, m: int, excl: int, T_train=None) -> tupl
     return picks, scores, nns
 
 
-def refine_dimension(T, j: int, m: int, excl: int, topk_excl: int | None = None) -> tuple:
-    """Refinement after Alg. 3: the top-1 discord (i, score, nn) of stream j's own self-join profile."""
-    P, I = mp_selfjoin(np.asarray(T, dtype=np.float64)[j], m, excl)
+def refine_dimension(T, j: int, m: int, excl: int, topk_excl: int | None = None, T_train=None) -> tuple:
+    """Refinement after Alg. 3: the top-1 discord (i, score, nn) of stream j's own self-join
+    profile or, with T_train, of its AB-join profile against training stream j."""
+    if T_train is None:
+        P, I = mp_selfjoin(np.asarray(T, dtype=np.float64)[j], m, excl)
+    else:
+        P, I = mp_abjoin(np.asarray(T, dtype=np.float64)[j], np.asarray(T_train, dtype=np.float64)[j], m)
     (i, _, score, nn), = discord_topk(P[None, :], I[None, :], 1, m if topk_excl is None else topk_excl)
     return i, score, nn
 

@@ -45,7 +45,7 @@ SIGNATURES = {
     "mp_backward": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _I32, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P]),
     "mp_abjoin": (_I32, [_P, _P, _P, _I32, _I32, _P, _P, _I32, _I32, _P, _P, _P, _P]),
     "dimension_detection": (_I32, [_P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _P,
-                                   _P, _P]),
+                                   _P, _P, _P, _P, _P]),
     "mp_selfjoin_static": (_I32, [_P, _I32, _I32, _I32, _P, _P, _P]),
 }
 

@@ -307,15 +307,24 @@ def exact_discords(T: torch.Tensor, series_len: Sequence[int], d: int, m: int, K
 
 
 def dimension_detection(T: torch.Tensor, R: torch.Tensor, series_len: Sequence[int], d: int, m: int, idx, grp,
-                        excl: int | None = None, all_scores: bool = False, gather: bool = False):
+                        excl: int | None = None, all_scores: bool = False, gather: bool = False,
+                        T_train: torch.Tensor | None = None, train_len: Sequence[int] | None = None):
     """Alg. 3: the raw dimension behind each sketch discord (idx, grp of discord_topk).
 
-    Returns {"dim", "score", "nn"} ([n_series, K]; score float64), plus
-    "scores" ([n_series, K, d], NaN outside the group) when all_scores and
-    "T_sel" (the chosen streams, packed like a K-stream sketch) when gather.
+    Self-join form by default; with T_train (and train_len) the train/test
+    form: each test window is scored against every window of the training
+    stream.  Returns {"dim", "score", "nn"} ([n_series, K]; score float64),
+    plus "scores" ([n_series, K, d], NaN outside the group) when all_scores
+    and "T_sel" (the chosen streams, packed like a K-stream sketch; with
+    T_train also "T_sel_train") when gather.
     """
     _need_cuda(T, R, idx, grp)
-    excl = default_excl(m) if excl is None else int(excl)
+    ab = T_train is not None
+    if ab:
+        _need_cuda(T_train)
+        if train_len is None or len(train_len) != len(series_len) or T_train.dtype != T.dtype:
+            raise ValueError("T_train needs train_len (one per series) and T's dtype")
+    excl = 0 if ab else (default_excl(m) if excl is None else int(excl))
     k = int(R.shape[1])
     ns = len(series_len)
     K = int(idx.shape[1])
@@ -325,30 +334,41 @@ def dimension_detection(T: torch.Tensor, R: torch.Tensor, series_len: Sequence[i
     nn = torch.empty((ns, K), dtype=torch.int32, device=dev)
     scores = torch.empty((ns, K, d), dtype=torch.float64, device=dev) if all_scores else None
     T_sel = torch.empty(sum(series_len) * K, dtype=T.dtype, device=dev) if gather else None
+    T_sel_t = torch.empty(sum(train_len) * K, dtype=T.dtype, device=dev) if (gather and ab) else None
     Rf = R if R.dtype == torch.float32 else R.float().contiguous()
     lens, lp = _i32_array(series_len)
+    tl, tlp = _i32_array(train_len) if ab else (None, None)
     h = _ctx(dev)
     N.check(N.lib().dimension_detection(h, _ptr(T), _dtype_code(T), ns, lp, d, _ptr(Rf), k, int(m), excl, K,
                                         _ptr(idx), _ptr(grp), _ptr(dim), _ptr(score), _ptr(nn),
-                                        _ptr(scores) if all_scores else None, _ptr(T_sel) if gather else None),
+                                        _ptr(scores) if all_scores else None, _ptr(T_sel) if gather else None,
+                                        _ptr(T_train) if ab else None, tlp if ab else None,
+                                        _ptr(T_sel_t) if T_sel_t is not None else None),
             h, "dimension_detection")
     out = {"dim": dim, "score": score, "nn": nn}
     if all_scores:
         out["scores"] = scores
     if gather:
         out["T_sel"] = T_sel
+        if ab:
+            out["T_sel_train"] = T_sel_t
     return out
 
 
 def refine_dimensions(T_sel: torch.Tensor, series_len: Sequence[int], K: int, m: int, excl: int | None = None,
-                      topk_excl: int | None = None, mp_precision: str = "fp32"):
-    """The refinement after Alg. 3: the top-1 discord of each chosen stream's own self-join profile.
+                      topk_excl: int | None = None, mp_precision: str = "fp32",
+                      T_sel_train: torch.Tensor | None = None, train_len: Sequence[int] | None = None):
+    """The refinement after Alg. 3: the top-1 discord of each chosen stream's own profile.
 
-    T_sel is dimension_detection(..., gather=True)["T_sel"]; returns
-    {"idx", "score", "nn"} of shape [n_series, K].
+    T_sel is dimension_detection(..., gather=True)["T_sel"]; with T_sel_train
+    (the train/test form) the profile is the AB join against the chosen
+    training stream.  Returns {"idx", "score", "nn"} of shape [n_series, K].
     """
     lens = [n for n in series_len for _ in range(K)]
-    P, I = mp_selfjoin(T_sel, lens, m, excl, precision=mp_precision)
+    if T_sel_train is None:
+        P, I = mp_selfjoin(T_sel, lens, m, excl, precision=mp_precision)
+    else:
+        P, I = mp_abjoin(T_sel, T_sel_train, lens, [n for n in train_len for _ in range(K)], m)
     idx, _, score, nn = discord_topk(P, I, lens, 1, m, 1, topk_excl)
     ns = len(series_len)
     return {"idx": idx.view(ns, K), "score": score.view(ns, K), "nn": nn.view(ns, K), "P": P, "I": I}

@@ -709,7 +709,9 @@ extern "C" TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, i
                                                   const int32_t* series_len_host, int32_t d, const float* R,
                                                   int32_t k, int32_t m, int32_t excl, int32_t K, const int32_t* idx,
                                                   const int32_t* grp, int32_t* dim, double* dim_score,
-                                                  int32_t* dim_nn, double* dim_scores, void* T_sel) {
+                                                  int32_t* dim_nn, double* dim_scores, void* T_sel,
+                                                  const void* T_train, const int32_t* train_len_host,
+                                                  void* T_sel_train) {
   tsk_status st = enter(ctx);
   if (st) return st;
   if (!T || !R || !idx || !grp || !dim || !dim_score || !dim_nn)
@@ -720,21 +722,30 @@ extern "C" TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, i
     return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: need n_series, d, k, K >= 1");
   if (m < 2 || m > 4096)
     return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: need 2 <= m <= 4096 (got %d)", m);
-  if (excl < 1) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: excl must be >= 1");
+  const bool ab = T_train != nullptr;
+  if (ab && !train_len_host)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: T_train needs train_len_host");
+  if (!ab && T_sel_train)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: T_sel_train needs T_train");
+  if (!ab && excl < 1) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "dimension_detection: excl must be >= 1");
   if ((st = check_lens(ctx, n_series, series_len_host, m, "dimension_detection"))) return st;
-  BatchLayout L{};
+  if (ab && (st = check_lens(ctx, n_series, train_len_host, m, "dimension_detection (train)"))) return st;
+  BatchLayout L{}, Lt{};
   if ((st = batch_layout(ctx, n_series, series_len_host, d, &L))) return st;
-  // scan items: (stream, chunk of windows) per series
+  const int32_t* scan_len = ab ? train_len_host : series_len_host;
+  if (ab && (st = batch_layout(ctx, n_series, train_len_host, d, &Lt))) return st;
+  if (!ab) Lt = L;
+  // scan items: (stream, chunk of windows) per series of the scanned side
   std::string key = "dims";
   const int32_t hdr[3] = {n_series, d, static_cast<int32_t>(tsk_dims_window_chunk())};
   append(key, hdr, 3);
   append(key, &m, 1);
-  append(key, series_len_host, n_series);
+  append(key, scan_len, n_series);
   const int64_t W = tsk_dims_window_chunk();
   const Blob* b = blob_get(ctx, key, [&](std::vector<char>& buf, std::vector<int64_t>& meta) {
     std::vector<int64_t> pre(static_cast<size_t>(n_series) + 1, 0);
     for (int s = 0; s < n_series; ++s) {
-      const int64_t l = static_cast<int64_t>(series_len_host[s]) - m + 1;
+      const int64_t l = static_cast<int64_t>(scan_len[s]) - m + 1;
       pre[s + 1] = pre[s] + static_cast<int64_t>(d) * ((l + W - 1) / W);
     }
     meta = {pre[n_series], 0};
@@ -744,8 +755,9 @@ extern "C" TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, i
   const int64_t total_items = b->meta[0];
   const int64_t* item_prefix = reinterpret_cast<const int64_t*>(static_cast<char*>(b->dev) + b->meta[1]);
   if ((st = tsk_ws_require(ctx, tsk_dims_ws_bytes(n_series, K, d, m)))) return st;
-  return tsk_launch_dims(ctx, T, t_dtype, n_series, L.cum, L.len, item_prefix, total_items, L.total_samples, d, R, k,
-                         m, excl, K, idx, grp, dim, dim_score, dim_nn, dim_scores, T_sel,
+  return tsk_launch_dims(ctx, T, ab ? T_train : T, t_dtype, n_series, L.cum, L.len, Lt.cum, Lt.len, item_prefix,
+                         total_items, L.total_samples, Lt.total_samples, d, R, k, m, ab ? 0 : excl, K, idx, grp, dim,
+                         dim_score, dim_nn, dim_scores, T_sel, ab ? T_sel_train : nullptr,
                          static_cast<char*>(ctx->ws));
 }
 

@@ -3,9 +3,10 @@
 //
 // For discord r of series s at window i* in sketch stream g*, every raw stream
 // j of the group J_g* = {j : R[j, g*] != 0} is scored by the 1NN distance of
-// its own window i* (Def. 6 at a single row, self-join exclusion |t - i*| <
-// excl), and j* is the first j (ascending) whose score exceeds every earlier
-// one, starting from 0.
+// its own window i* (Def. 6 at a single row: self-join exclusion |t - i*| <
+// excl, or, in the train/test form, against every window of the training
+// series' stream j), and j* is the first j (ascending) whose score exceeds
+// every earlier one, starting from 0.
 //
 // Pipeline per call:
 //   1. k_dd_query   one warp per (series, discord, stream of its group): the
@@ -40,8 +41,10 @@ constexpr int kTW = kScanThreads * kWinPerThread;     // 2048 windows per scan i
 constexpr double kConstRelVar = 1e-12;
 
 struct DimArgs {
-  const int64_t* cum;          // [n_series + 1] sample offsets of series (per stream)
+  const int64_t* cum;          // [n_series + 1] sample offsets of series (per stream): the queried series
   const int32_t* len;          // [n_series]
+  const int64_t* cum_t;        // scanned series (the training series in the AB form; else = cum)
+  const int32_t* len_t;
   const int64_t* item_prefix;  // [n_series + 1] scan items before each series
   const float* R;              // d x k
   const int32_t* idx;          // n_series x K
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kScanThreads) k_dd_scan(const TX* __restrict__
 
   for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     const int s = tsk_find_segment<int64_t>(a.item_prefix, a.n_series, item);
-    const int n = a.len[s];
+    const int n = a.len_t[s];
     const int l = n - m + 1;
     const int chunks = (l + kTW - 1) / kTW;
     const int64_t rem = item - a.item_prefix[s];
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kScanThreads) k_dd_scan(const TX* __restrict__
       }
     }
     if (!any) continue;
-    const TX* x = T + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n + t0;
+    const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n + t0;
 
     // ---- stage the chunk shifted by its first sample; float-float prefix sums ----
     const TX x_ref = x[0];
@@ -363,7 +366,8 @@ __device__ void window_mean_const(const TX* x, int i, int m, double* mean, bool*
 }
 
 template <typename TX>
-__global__ void __launch_bounds__(256) k_dd_select(const TX* __restrict__ T, DimArgs a, int32_t* __restrict__ dim,
+__global__ void __launch_bounds__(256) k_dd_select(const TX* __restrict__ Tq, const TX* __restrict__ T, DimArgs a,
+                                                   int32_t* __restrict__ dim,
                                                    double* __restrict__ dim_score, int32_t* __restrict__ dim_nn,
                                                    double* __restrict__ dim_scores) {
   const int64_t wid = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -386,7 +390,8 @@ __global__ void __launch_bounds__(256) k_dd_select(const TX* __restrict__ T, Dim
     double sc = NAN;
     int nn = -1;
     if (valid && a.R[static_cast<int64_t>(j) * a.k + g_star] != 0.f) {
-      const TX* x = T + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n;
+      const TX* xq = Tq + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n;
+      const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * a.len_t[s];
       const unsigned long long p = a.best[wid * a.d + j];
       if (p == 0ull) {
         sc = INFINITY;  // no admissible neighbour
@@ -394,12 +399,12 @@ __global__ void __launch_bounds__(256) k_dd_select(const TX* __restrict__ T, Dim
         nn = tsk_unpack_idx(p);
         double mq, mt;
         bool cq, ct;
-        window_mean_const(x, i_star, a.m, &mq, &cq);
+        window_mean_const(xq, i_star, a.m, &mq, &cq);
         window_mean_const(x, nn, a.m, &mt, &ct);
         if (cq) sc = ct ? 0.0 : sqm;
         else if (ct) sc = sqm;
         else {
-          const double rho = tsk::window_rho(x, i_star, nn, a.m, mq, mt);
+          const double rho = tsk::window_rho(xq, i_star, x, nn, a.m, mq, mt);
           sc = sqrt(fmax(0.0, m2 * (1.0 - rho)));
         }
       }
@@ -458,8 +463,9 @@ size_t scan_smem_bytes(int m) {
 }
 
 template <typename TX>
-tsk_status run_dims(tsk_ctx* ctx, const TX* T, const DimArgs& a, int64_t total_items, int32_t* dim, double* dim_score,
-                    int32_t* dim_nn, double* dim_scores, TX* T_sel, int64_t total_samples) {
+tsk_status run_dims(tsk_ctx* ctx, const TX* T, const TX* Tt, const DimArgs& a, int64_t total_items, int32_t* dim,
+                    double* dim_score, int32_t* dim_nn, double* dim_scores, TX* T_sel, TX* T_sel_t,
+                    int64_t total_samples, int64_t total_samples_t) {
   cudaStream_t st = ctx->stream;
   const int64_t triples = static_cast<int64_t>(a.n_series) * a.K * a.d;
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(a.best, 0, sizeof(unsigned long long) * static_cast<size_t>(triples), st));
@@ -473,11 +479,11 @@ tsk_status run_dims(tsk_ctx* ctx, const TX* T, const DimArgs& a, int64_t total_i
     TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dd_scan<TX>, kScanThreads, smem));
     const int64_t grid = std::min<int64_t>(total_items, static_cast<int64_t>(std::max(per_sm, 1)) * ctx->sm_count);
     tsk_prof_scope ps(ctx, TSK_PROF_DIMS);
-    k_dd_scan<TX><<<static_cast<unsigned>(grid), kScanThreads, smem, st>>>(T, a, total_items);
+    k_dd_scan<TX><<<static_cast<unsigned>(grid), kScanThreads, smem, st>>>(Tt, a, total_items);
     TSK_LAUNCH_CHECK(ctx, "k_dd_scan");
   }
   const int64_t warps = static_cast<int64_t>(a.n_series) * a.K;
-  k_dd_select<TX><<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(T, a, dim, dim_score, dim_nn,
+  k_dd_select<TX><<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(T, Tt, a, dim, dim_score, dim_nn,
                                                                                      dim_scores);
   TSK_LAUNCH_CHECK(ctx, "k_dd_select");
   if (T_sel && total_samples > 0) {
@@ -487,6 +493,13 @@ tsk_status run_dims(tsk_ctx* ctx, const TX* T, const DimArgs& a, int64_t total_i
                                                                      T_sel);
     TSK_LAUNCH_CHECK(ctx, "k_dd_gather");
   }
+  if (T_sel_t && total_samples_t > 0) {
+    const int64_t total = total_samples_t * a.K;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, static_cast<int64_t>(ctx->sm_count) * 16);
+    k_dd_gather<TX><<<static_cast<unsigned>(blocks), 256, 0, st>>>(Tt, a.cum_t, a.len_t, dim, a.n_series, a.d, a.K,
+                                                                     total, T_sel_t);
+    TSK_LAUNCH_CHECK(ctx, "k_dd_gather");
+  }
   return TSK_OK;
 }
 
@@ -494,14 +507,17 @@ tsk_status run_dims(tsk_ctx* ctx, const TX* T, const DimArgs& a, int64_t total_i
 
 int tsk_dims_window_chunk() { return kTW; }
 
-tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_series, const int64_t* d_cum,
-                           const int32_t* d_len, const int64_t* d_item_prefix, int64_t total_items,
-                           int64_t total_samples, int32_t d, const float* R, int32_t k, int32_t m, int32_t excl,
+tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, const void* T_train, int t_dtype, int32_t n_series,
+                           const int64_t* d_cum, const int32_t* d_len, const int64_t* d_cum_t, const int32_t* d_len_t,
+                           const int64_t* d_item_prefix, int64_t total_items, int64_t total_samples,
+                           int64_t total_samples_t, int32_t d, const float* R, int32_t k, int32_t m, int32_t excl,
                            int32_t K, const int32_t* idx, const int32_t* grp, int32_t* dim, double* dim_score,
-                           int32_t* dim_nn, double* dim_scores, void* T_sel, char* ws) {
+                           int32_t* dim_nn, double* dim_scores, void* T_sel, void* T_sel_train, char* ws) {
   DimArgs a;
   a.cum = d_cum;
   a.len = d_len;
+  a.cum_t = d_cum_t;
+  a.len_t = d_len_t;
   a.item_prefix = d_item_prefix;
   a.R = R;
   a.idx = idx;
@@ -519,10 +535,12 @@ tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_s
   a.excl = excl;
   a.K = K;
   if (t_dtype == TSK_F64)
-    return run_dims<double>(ctx, static_cast<const double*>(T), a, total_items, dim, dim_score, dim_nn, dim_scores,
-                            static_cast<double*>(T_sel), total_samples);
-  return run_dims<float>(ctx, static_cast<const float*>(T), a, total_items, dim, dim_score, dim_nn, dim_scores,
-                         static_cast<float*>(T_sel), total_samples);
+    return run_dims<double>(ctx, static_cast<const double*>(T), static_cast<const double*>(T_train), a, total_items,
+                            dim, dim_score, dim_nn, dim_scores, static_cast<double*>(T_sel),
+                            static_cast<double*>(T_sel_train), total_samples, total_samples_t);
+  return run_dims<float>(ctx, static_cast<const float*>(T), static_cast<const float*>(T_train), a, total_items, dim,
+                         dim_score, dim_nn, dim_scores, static_cast<float*>(T_sel), static_cast<float*>(T_sel_train),
+                         total_samples, total_samples_t);
 }
 
 size_t tsk_dims_ws_bytes(int32_t n_series, int32_t K, int32_t d, int32_t m) {

@@ -204,11 +204,12 @@ tsk_status tsk_launch_topk(tsk_ctx* ctx, const void* P, int p_dtype, const int32
 // Dimension detection (Alg. 3) and the gather of the chosen streams.
 int tsk_dims_window_chunk();
 size_t tsk_dims_ws_bytes(int32_t n_series, int32_t K, int32_t d, int32_t m);
-tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_series, const int64_t* d_cum,
-                           const int32_t* d_len, const int64_t* d_item_prefix, int64_t total_items,
-                           int64_t total_samples, int32_t d, const float* R, int32_t k, int32_t m, int32_t excl,
+tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, const void* T_train, int t_dtype, int32_t n_series,
+                           const int64_t* d_cum, const int32_t* d_len, const int64_t* d_cum_t, const int32_t* d_len_t,
+                           const int64_t* d_item_prefix, int64_t total_items, int64_t total_samples,
+                           int64_t total_samples_t, int32_t d, const float* R, int32_t k, int32_t m, int32_t excl,
                            int32_t K, const int32_t* idx, const int32_t* grp, int32_t* dim, double* dim_score,
-                           int32_t* dim_nn, double* dim_scores, void* T_sel, char* ws);
+                           int32_t* dim_nn, double* dim_scores, void* T_sel, void* T_sel_train, char* ws);
 // Adjoint.
 tsk_status tsk_launch_backward(tsk_ctx* ctx, const float* dscore, const int32_t* idx, const int32_t* grp,
                                const int32_t* nn, int32_t K, const void* T, int t_dtype, const double* stats,

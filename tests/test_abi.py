@@ -60,4 +60,4 @@ def test_null_context_is_rejected(libpath):
 def test_dimension_detection_rejects_a_null_context(libpath):
     lib = _native.lib()
     assert lib.dimension_detection(None, None, 0, 0, None, 0, None, 0, 0, 0, 0, None, None, None, None, None,
-                                   None, None) == 1
+                                   None, None, None, None, None) == 1

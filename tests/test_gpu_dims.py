@@ -28,12 +28,13 @@ def tsk():
     return t
 
 
-def _check_dims(series, R, queries, m, excl, got, rel=MP_REL_TOL):
+def _check_dims(series, R, queries, m, excl, got, rel=MP_REL_TOL, train=None):
     """Compare GPU outputs for one series with the oracle's Alg. 3 on the same (i*, g*) queries."""
     T = np.asarray(series, dtype=np.float64)
+    Tn = T if train is None else np.asarray(train, dtype=np.float64)
     fl = d_floor(m)
     valid = [(i, g) for (i, g) in queries if i >= 0]
-    picks, scores, nns = o.dimension_detection(T, R, valid, m, excl)
+    picks, scores, nns = o.dimension_detection(T, R, valid, m, excl, T_train=train)
     q = 0
     for r, (i, g) in enumerate(queries):
         if i < 0:
@@ -61,20 +62,26 @@ def _check_dims(series, R, queries, m, excl, got, rel=MP_REL_TOL):
             assert within_mp_tol(got["score"][r], s_ref, m, rel)
             nn_gpu = int(got["nn"][r])
             if nn_gpu != nn_ref:  # the neighbour must be an equally near window
-                dd = o.window_distance(T[j_ref], i, nn_gpu, m) if nn_gpu >= 0 else math.inf
-                assert abs(i - nn_gpu) >= excl and within_mp_tol(dd, s_ref, m, rel)
+                Zq, _, _, _ = o.znorm_windows(T[j_ref], m)
+                Zt, _, _, _ = o.znorm_windows(Tn[j_ref], m)
+                dd = float(np.linalg.norm(Zq[i] - Zt[nn_gpu])) if nn_gpu >= 0 else math.inf
+                assert (train is not None or abs(i - nn_gpu) >= excl) and within_mp_tol(dd, s_ref, m, rel)
         q += 1
 
 
-def _run(tsk, Ts, R, queries, m, excl, dtype=torch.float32, gather=False):
-    """Ts: list of (d, n_s) arrays; queries: per series list of K (i*, g*)."""
+def _run(tsk, Ts, R, queries, m, excl, dtype=torch.float32, gather=False, train=None):
+    """Ts: list of (d, n_s) arrays; queries: per series list of K (i*, g*); train: list like Ts."""
     d = Ts[0].shape[0]
     T = torch.cat([torch.as_tensor(np.ascontiguousarray(t)).reshape(-1) for t in Ts]).to("cuda", dtype)
     lens = [t.shape[1] for t in Ts]
     idx = torch.tensor([[i for i, _ in qs] for qs in queries], dtype=torch.int32, device="cuda")
     grp = torch.tensor([[g for _, g in qs] for qs in queries], dtype=torch.int32, device="cuda")
+    Tt, tl = None, None
+    if train is not None:
+        Tt = torch.cat([torch.as_tensor(np.ascontiguousarray(t)).reshape(-1) for t in train]).to("cuda", dtype)
+        tl = [t.shape[1] for t in train]
     res = tsk.dimension_detection(T, torch.as_tensor(R, dtype=torch.float32).cuda(), lens, d, m, idx, grp, excl,
-                                  all_scores=True, gather=gather)
+                                  all_scores=True, gather=gather, T_train=Tt, train_len=tl)
     tsk.sync()
     return T, lens, {k: v.cpu().numpy() for k, v in res.items()}
 
@@ -175,3 +182,30 @@ def test_full_size_water_dimensions(tsk):
     queries += [(int(rng.integers(0, n - m + 1)), int(rng.integers(0, k))) for _ in range(3)]
     _, _, got = _run(tsk, [T], wl.R, [queries], m, excl)
     _check_dims(T, wl.R, queries, m, excl, {key: v[0] for key, v in got.items()})
+
+
+def test_train_test_form_every_score_and_the_ab_refinement(tsk):
+    """Alg. 3 as printed: test windows scored against every window of the training streams."""
+    rng = np.random.default_rng(71)
+    d, k, m = 8, 3, 40
+    test_lens, train_lens = [2500, 900], [1800, 3100]
+    test = [np.cumsum(rng.normal(size=(d, n)), axis=1) for n in test_lens]
+    train = [np.cumsum(rng.normal(size=(d, n)), axis=1) for n in train_lens]
+    R = synth.gaussian_R(d, k, 9)
+    queries = [[(int(rng.integers(0, n - m + 1)), int(rng.integers(0, k))) for _ in range(3)] for n in test_lens]
+    for dtype in (torch.float32, torch.float64):
+        _, _, got = _run(tsk, test, R, queries, m, 0, dtype=dtype, gather=(dtype == torch.float64), train=train)
+        for s in range(2):
+            _check_dims(test[s], R, queries[s], m, 0, {key: v[s] for key, v in got.items()}, train=train[s])
+    # gather + AB refinement (float64 input, float32 AB profile)
+    ref = tsk.refine_dimensions(torch.as_tensor(got["T_sel"]).cuda(), test_lens, 3, m,
+                                T_sel_train=torch.as_tensor(got["T_sel_train"]).cuda(), train_len=train_lens)
+    tsk.sync()
+    for s in range(2):
+        for r in range(3):
+            j = int(got["dim"][s][r])
+            i, score, nn = o.refine_dimension(test[s], j, m, 0, T_train=train[s])
+            A, _ = o.mp_abjoin(test[s][j], train[s][j], m)
+            gi = int(ref["idx"][s, r])
+            assert gi == i or A[gi] >= (1 - 1e-3) * A[i]
+            assert within_mp_tol(float(ref["score"][s, r]), score, m)

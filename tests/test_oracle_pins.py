@@ -499,3 +499,15 @@ def test_ab_identity_count_sketch_gives_the_exact_ab_profiles():
     _, Pe, Ie = o.ab_discords(test, train, m, 2, m)
     np.testing.assert_allclose(Ps, Pe, rtol=1e-9, atol=1e-9)
     np.testing.assert_array_equal(Is, Ie)
+
+
+def test_ab_refinement_is_the_brute_force_ab_discord_of_the_stream():
+    rng = np.random.default_rng(45)
+    train = np.cumsum(rng.normal(size=(2, 160)), axis=1)
+    test = np.cumsum(rng.normal(size=(2, 120)), axis=1)
+    m = 12
+    i, score, nn = o.refine_dimension(test, 1, m, 0, T_train=train)
+    Za, Zb = _zscore_windows_scipy(test[1], m), _zscore_windows_scipy(train[1], m)
+    best = [min((float(np.linalg.norm(Za[t] - Zb[u])), u) for u in range(len(Zb))) for t in range(len(Za))]
+    ib = max(range(len(best)), key=lambda t: (best[t][0], -t))
+    assert i == ib and abs(score - best[ib][0]) <= 1e-9 and nn == best[ib][1]
