@@ -20,7 +20,8 @@ Time Series for Fast Discord Mining" (arXiv 2311.03393) defines:
                the 1NN distance of that window in every raw stream j of the
                group J_g*, keep the largest; then the optional refinement
                (a whole self-join profile of the chosen stream)
-  * Sec. III-C dimension addition/deletion by linearity of the sketch
+  * Sec. III-C dimension addition/deletion by linearity of the sketch, and the
+               point update (one sample of one dimension changes by delta)
   * the adjoint of the top-K aggregated discord scores (not in the paper; the
     derivative of the same definitions, checked against central differences)
 
@@ -44,6 +45,10 @@ Readings where the paper is silent (the same readings the CUDA path takes):
     starting from 0; when no score exceeds 0, the lowest j of J_g* (score 0);
     an empty J_g* gives j* = -1.  Refinement = the top-1 discord of T_j*'s
     own self-join profile.
+  * point update: the stream's global normalisation (mean, sigma) of the
+    build is held fixed, so T_j[i] += delta moves sketch stream g at time i
+    by R[j, g] * delta / sigma_j (Alg. 1's s(j) delta for a count sketch and
+    unit sigma).
   * AB join: train and test are each z-normalised over their own length
     before sketching ("respectively", Sec. III-A), sketched with the same R;
     every training window is a candidate (no exclusion), lowest j on ties.
@@ -472,3 +477,13 @@ def ab_discords(T_test, T_train, m: int, K: int, topk_excl: int, R=None, bf16: b
         Is.append(I)
     P, I = np.array(Ps), np.array(Is)
     return discord_topk(P, I, K, topk_excl), P, I
+
+
+def point_update(S, R, sigma, updates) -> np.ndarray:
+    """Sec. III-C point update: for each (j, i, delta), T_j[i] += delta moves every
+    sketch stream g at time i by R[j, g] * delta / sigma_j (sigma_j of the build)."""
+    S = np.array(S, dtype=np.float64, copy=True)
+    R = np.asarray(R, dtype=np.float64)
+    for j, i, delta in updates:
+        S[:, i] += R[j, :] * (delta / sigma[j])
+    return S

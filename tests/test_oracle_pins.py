@@ -511,3 +511,23 @@ def test_ab_refinement_is_the_brute_force_ab_discord_of_the_stream():
     best = [min((float(np.linalg.norm(Za[t] - Zb[u])), u) for u in range(len(Zb))) for t in range(len(Za))]
     ib = max(range(len(best)), key=lambda t: (best[t][0], -t))
     assert i == ib and abs(score - best[ib][0]) <= 1e-9 and nn == best[ib][1]
+
+
+def test_point_update_equals_sketching_the_updated_series_with_the_build_normalisation():
+    rng = np.random.default_rng(46)
+    d, n, k = 7, 300, 3
+    T = np.cumsum(rng.normal(size=(d, n)), axis=1)
+    R = synth.gaussian_R(d, k, 4)
+    Tbar, mu, sigma = o.global_znorm(T)
+    S = o.sketch(Tbar, R)
+    ups = [(2, 10, 0.5), (2, 10, -1.25), (6, 299, 3.0), (0, 0, -2.0)]   # repeated point included
+    T2 = T.copy()
+    for j, i, dl in ups:
+        T2[j, i] += dl
+    want = R.T @ ((T2 - mu[:, None]) / sigma[:, None])
+    np.testing.assert_allclose(o.point_update(S, R, sigma, ups), want, rtol=0, atol=1e-12)
+    # a count sketch moves only stream h(j), by s(j) delta / sigma_j
+    h, sg = synth.count_sketch_hashes(d, k, 5)
+    Rc = synth.count_sketch_R(d, k, 5)
+    D = o.point_update(np.zeros((k, n)), Rc, sigma, [(4, 50, 1.0)])
+    assert np.count_nonzero(D) == 1 and D[h[4], 50] == pytest.approx(sg[4] / sigma[4])
