@@ -159,6 +159,31 @@ TSK_API tsk_status ts_sketch_update_dims(tsk_ctx* ctx, void* S, const void* T_di
                                          int32_t precision, double* stats, uint8_t* dirty_host);
 
 /*
+ * ts_sketch_point_update - point updates (Sec. III-C): sample t of dimension
+ * j of series s changes by delta, and the sketch follows by linearity,
+ * S_g[t] += R[j][g] * delta / sigma_j for every g (Alg. 1's s(j) delta for a
+ * count sketch), with the build's normalisation (mean, sigma in stats) held
+ * fixed.
+ *   S, stats, R : the ts_sketch_build outputs/inputs (S of `precision`'s type).
+ *   T           : optional (NULL to skip) device batch layout of the series;
+ *                 when given it is updated in place and S moves by R[j][g]
+ *                 times the change of the stored sample's normalised value (in
+ *                 TSK_SKETCH_BF16 mode: of its bfloat16 rounding), so S stays
+ *                 the sketch of the updated T.  Required for TSK_SKETCH_BF16.
+ *   upd_*_host  : n_upd host arrays (series, dimension, time, delta); repeated
+ *                 points are merged (deltas summed).  The arrays are read
+ *                 before the call returns.
+ * The changed sketch streams need a new profile (mp_selfjoin or mp_abjoin).
+ * Errors: TSK_ERR_INVALID_ARG for NULL arrays, a bad dtype or precision, an
+ * update out of range or a non-finite delta; nothing is changed then.
+ */
+TSK_API tsk_status ts_sketch_point_update(tsk_ctx* ctx, void* S, void* T, int32_t t_dtype, int32_t n_series,
+                                          const int32_t* series_len_host, int32_t d, const float* R, int32_t k,
+                                          int32_t precision, const double* stats, int32_t n_upd,
+                                          const int32_t* upd_series_host, const int32_t* upd_dim_host,
+                                          const int32_t* upd_time_host, const double* upd_delta_host);
+
+/*
  * mp_selfjoin - self-join matrix profile of every stream (Def. 6 with
  * T_test = T_train; Def. 3 z-normalised Euclidean distance).
  *

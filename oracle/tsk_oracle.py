@@ -487,3 +487,12 @@ def point_update(S, R, sigma, updates) -> np.ndarray:
     for j, i, delta in updates:
         S[:, i] += R[j, :] * (delta / sigma[j])
     return S
+
+
+def znorm_with(T, mu, sigma) -> np.ndarray:
+    """T_bar under given per-stream statistics (the build's, for point updates): (T - mu) / sigma, 0 where sigma = 0."""
+    T = np.asarray(T, dtype=np.float64)
+    out = np.zeros_like(T)
+    live = np.asarray(sigma) > 0
+    out[live] = (T[live] - np.asarray(mu)[live, None]) / np.asarray(sigma)[live, None]
+    return out

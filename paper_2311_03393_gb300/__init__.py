@@ -25,5 +25,6 @@ from .api import (  # noqa: F401
     sketched_discords,
     sync,
     ts_sketch_build,
+    ts_sketch_point_update,
     ts_sketch_update_dims,
 )

@@ -43,6 +43,7 @@ SIGNATURES = {
     "mp_selfjoin": (_I32, [_P, _P, _I32, _I32, _P, _P, _I32, _I32, _I32, _P, _P]),
     "discord_topk": (_I32, [_P, _P, _I32, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P]),
     "mp_backward": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _I32, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P]),
+    "ts_sketch_point_update": (_I32, [_P, _P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, _P, _I32, _P, _P, _P, _P]),
     "mp_abjoin": (_I32, [_P, _P, _P, _I32, _I32, _P, _P, _I32, _I32, _P, _P, _P, _P]),
     "dimension_detection": (_I32, [_P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _P,
                                    _P, _P, _P, _P, _P]),

@@ -118,6 +118,33 @@ def ts_sketch_update_dims(S: torch.Tensor, T_dims: torch.Tensor, series_len: Seq
     return dirty, stats
 
 
+def ts_sketch_point_update(S: torch.Tensor, stats: torch.Tensor, R: torch.Tensor, series_len: Sequence[int], d: int,
+                           series, dims, times, deltas, T: torch.Tensor | None = None, precision: str = "bf16"):
+    """Point updates T_j[t] += delta of (series, dim, time, delta) lists, and the sketch by linearity (Sec. III-C).
+
+    With T, T is updated in place too and S stays the sketch of the updated T
+    (required for the bf16-matched sketch).  The build's normalisation is kept.
+    """
+    _need_cuda(S, stats, R)
+    if T is not None:
+        _need_cuda(T)
+    k = int(R.shape[1])
+    ns = len(series_len)
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32)) for a in (series, dims, times)]
+    dl = np.ascontiguousarray(np.asarray(deltas, dtype=np.float64))
+    n_upd = len(dl)
+    if any(len(a) != n_upd for a in arrs):
+        raise ValueError("series, dims, times and deltas must have the same length")
+    Rf = R if R.dtype == torch.float32 else R.float().contiguous()
+    lens, lp = _i32_array(series_len)
+    h = _ctx(S.device)
+    tcode = _dtype_code(T) if T is not None else N.TSK_F32
+    N.check(N.lib().ts_sketch_point_update(h, _ptr(S), _ptr(T) if T is not None else None, tcode, ns, lp, d,
+                                           _ptr(Rf), k, SKETCH_PRECISION[precision], _ptr(stats), n_upd,
+                                           *(a.ctypes.data_as(C.c_void_p) for a in arrs),
+                                           dl.ctypes.data_as(C.c_void_p)), h, "ts_sketch_point_update")
+
+
 def mp_selfjoin(X: torch.Tensor, stream_len: Sequence[int], m: int, excl: int | None = None,
                 precision: str = "fp32", mask=None, P: torch.Tensor | None = None,
                 I: torch.Tensor | None = None, tile_rows: int | None = None):

@@ -3,6 +3,8 @@
 #include "tsk_internal.cuh"
 
 #include <algorithm>
+#include <array>
+#include <cmath>
 #include <chrono>
 #include <cstdarg>
 #include <cstring>
@@ -643,6 +645,62 @@ extern "C" TSK_API tsk_status ts_sketch_update_dims(tsk_ctx* ctx, void* S, const
       dirty_host[g] = f;
     }
   return TSK_OK;
+}
+
+extern "C" TSK_API tsk_status ts_sketch_point_update(tsk_ctx* ctx, void* S, void* T, int32_t t_dtype,
+                                                     int32_t n_series, const int32_t* series_len_host, int32_t d,
+                                                     const float* R, int32_t k, int32_t precision, const double* stats,
+                                                     int32_t n_upd, const int32_t* upd_series_host,
+                                                     const int32_t* upd_dim_host, const int32_t* upd_time_host,
+                                                     const double* upd_delta_host) {
+  tsk_status st = enter(ctx);
+  if (st) return st;
+  if (!S || !R || !stats) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_point_update: S, R, stats must be non-NULL");
+  if (t_dtype != TSK_F32 && t_dtype != TSK_F64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "bad t_dtype");
+  if (precision < TSK_SKETCH_BF16 || precision > TSK_SKETCH_FP64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "bad precision");
+  if (precision == TSK_SKETCH_BF16 && !T)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_point_update: the bf16-matched sketch needs T (old samples)");
+  if (n_series < 1 || d < 1 || k < 1 || n_upd < 0)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_point_update: need n_series, d, k >= 1 and n_upd >= 0");
+  if (n_upd == 0) return TSK_OK;
+  if (!upd_series_host || !upd_dim_host || !upd_time_host || !upd_delta_host)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_point_update: update arrays must be non-NULL");
+  if ((st = check_lens(ctx, n_series, series_len_host, 1, "ts_sketch_point_update"))) return st;
+  // distinct points, deltas of repeated points summed in the given order
+  std::vector<std::pair<std::array<int32_t, 3>, double>> pts;
+  pts.reserve(n_upd);
+  for (int32_t u = 0; u < n_upd; ++u) {
+    const int32_t s = upd_series_host[u], j = upd_dim_host[u], t = upd_time_host[u];
+    if (s < 0 || s >= n_series || j < 0 || j >= d || t < 0 || t >= series_len_host[s])
+      return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_point_update: update %d (%d, %d, %d) out of range", u, s, j, t);
+    if (!std::isfinite(upd_delta_host[u]))
+      return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_point_update: delta %d is not finite", u);
+    pts.push_back({{s, j, t}, upd_delta_host[u]});
+  }
+  std::stable_sort(pts.begin(), pts.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::vector<int4> up;
+  std::vector<double> dl;
+  for (size_t u = 0; u < pts.size(); ++u) {
+    if (!up.empty() && up.back().x == pts[u].first[0] && up.back().y == pts[u].first[1] &&
+        up.back().z == pts[u].first[2]) {
+      dl.back() += pts[u].second;
+    } else {
+      up.push_back(make_int4(pts[u].first[0], pts[u].first[1], pts[u].first[2], 0));
+      dl.push_back(pts[u].second);
+    }
+  }
+  BatchLayout L{};
+  if ((st = batch_layout(ctx, n_series, series_len_host, d, &L))) return st;
+  const size_t np = up.size();
+  if ((st = tsk_ws_require(ctx, tsk_carver::bytes_for(np, sizeof(int4)) + tsk_carver::bytes_for(np, 8)))) return st;
+  tsk_carver cv(ctx->ws);
+  int4* d_pts = cv.take<int4>(np);
+  double* d_dl = cv.take<double>(np);
+  TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_pts, up.data(), sizeof(int4) * np, cudaMemcpyHostToDevice, ctx->stream));
+  TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_dl, dl.data(), sizeof(double) * np, cudaMemcpyHostToDevice, ctx->stream));
+  // (copies from pageable memory return once staged, so the vectors may go out of scope)
+  return tsk_launch_point_update(ctx, S, T, t_dtype, d_pts, d_dl, static_cast<int32_t>(np), L.cum, L.len, d, R, k,
+                                 precision, stats);
 }
 
 extern "C" TSK_API tsk_status mp_selfjoin(tsk_ctx* ctx, const void* X, int32_t x_dtype, int32_t n_streams,

@@ -186,6 +186,10 @@ tsk_status tsk_launch_update_dims(tsk_ctx* ctx, void* S, const void* T_dims, int
                                   const int64_t* d_cum, const int32_t* d_len, int64_t total_samples, int32_t nd,
                                   const float* d_Rrows, const int8_t* d_op, int32_t k, int32_t precision,
                                   const double* stats);
+// Point updates of T and S (distinct points; see tsk_sketch.cu).
+tsk_status tsk_launch_point_update(tsk_ctx* ctx, void* S, void* T, int t_dtype, const int4* d_pts, const double* d_delta,
+                                   int32_t npts, const int64_t* d_cum, const int32_t* d_len, int32_t d, const float* R,
+                                   int32_t k, int32_t precision, const double* stats);
 // Matrix profile pipeline (window stats, diagonal kernel, refinement).
 tsk_status tsk_run_mp(tsk_ctx* ctx, const void* X, int x_dtype, int32_t n_streams, const tsk_mp_plan& plan,
                       int32_t m, int32_t excl, int32_t precision, void* P, int32_t* I, char* ws);

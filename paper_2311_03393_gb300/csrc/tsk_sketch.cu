@@ -267,6 +267,56 @@ __global__ void k_update_dims(Acc* __restrict__ S, const TIn* __restrict__ Td, c
   }
 }
 
+// ---------------------------------------------------------------------------
+// Point updates T_j[t] += delta (Sec. III-C), the build's normalisation held
+// fixed; one thread per distinct point.  With T given, T is updated in place
+// and S moves by R[j,g] times the change of the normalised stored sample (in
+// bf16-matched mode: of its bfloat16 rounding), so S stays the sketch of the
+// updated series; without T, by R[j,g] * delta / sigma_j.
+// ---------------------------------------------------------------------------
+template <typename TX, typename Acc>
+__global__ void k_point_update(Acc* __restrict__ S, TX* __restrict__ T, const int4* __restrict__ pts,
+                               const double* __restrict__ delta, int32_t npts, const int64_t* __restrict__ cum,
+                               const int32_t* __restrict__ len, int32_t d, const float* __restrict__ R, int32_t k,
+                               int32_t precision, const double* __restrict__ stats) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= npts) return;
+  const int4 p = pts[u];
+  const int s = p.x, j = p.y, t = p.z;
+  const int n = len[s];
+  const int64_t st = 2 * (static_cast<int64_t>(s) * d + j);
+  const double mu = stats[st], sg = stats[st + 1];
+  const double ri = sg > 0.0 ? 1.0 / sg : 0.0;
+  Acc* srow = S + static_cast<int64_t>(k) * cum[s] + t;
+  if (T) {
+    const int64_t pos = cum[s] * d + static_cast<int64_t>(j) * n + t;
+    const TX x_old = T[pos];
+    const TX x_new = static_cast<TX>(static_cast<double>(x_old) + delta[u]);
+    T[pos] = x_new;
+    if (precision == TSK_SKETCH_BF16) {
+      const NormC c = make_normc(mu, ri);
+      const float a = tsk_bf16_bits_to_f32(tbar_bf16(x_old, c));
+      const float b = tsk_bf16_bits_to_f32(tbar_bf16(x_new, c));
+      for (int g = 0; g < k; ++g) {
+        const float r = tsk_bf16_bits_to_f32(tsk_f64_to_bf16_bits(static_cast<double>(R[j * k + g])));
+        if (r != 0.f && a != b) atomicAdd(&srow[static_cast<int64_t>(g) * n], static_cast<Acc>(__fmaf_rn(r, b, -(r * a))));
+      }
+    } else {
+      const double dt = tsk_tbar(static_cast<double>(x_new), mu, ri) - tsk_tbar(static_cast<double>(x_old), mu, ri);
+      for (int g = 0; g < k; ++g) {
+        const double r = static_cast<double>(R[j * k + g]);
+        if (r != 0.0) atomicAdd(&srow[static_cast<int64_t>(g) * n], static_cast<Acc>(r * dt));
+      }
+    }
+  } else {
+    const double dt = delta[u] * ri;
+    for (int g = 0; g < k; ++g) {
+      const double r = static_cast<double>(R[j * k + g]);
+      if (r != 0.0) atomicAdd(&srow[static_cast<int64_t>(g) * n], static_cast<Acc>(r * dt));
+    }
+  }
+}
+
 }  // namespace
 
 tsk_status tsk_launch_colstats(tsk_ctx* ctx, const void* T, int t_dtype, const int64_t* d_off, const int32_t* d_len,
@@ -334,5 +384,31 @@ tsk_status tsk_launch_update_dims(tsk_ctx* ctx, void* S, const void* T_dims, int
       k_update_dims<float, float><<<static_cast<unsigned>(blocks), threads, 0, ctx->stream>>>(static_cast<float*>(S), static_cast<const float*>(T_dims), d_cum, d_len, n_series, total_samples, nd, d_Rrows, d_op, k, precision, stats);
   }
   TSK_LAUNCH_CHECK(ctx, "k_update_dims");
+  return TSK_OK;
+}
+
+tsk_status tsk_launch_point_update(tsk_ctx* ctx, void* S, void* T, int t_dtype, const int4* d_pts, const double* d_delta,
+                                   int32_t npts, const int64_t* d_cum, const int32_t* d_len, int32_t d, const float* R,
+                                   int32_t k, int32_t precision, const double* stats) {
+  if (npts <= 0) return TSK_OK;
+  const unsigned blocks = static_cast<unsigned>((npts + 127) / 128);
+  cudaStream_t st = ctx->stream;
+  const bool f64s = precision == TSK_SKETCH_FP64;
+  if (t_dtype == TSK_F64) {
+    if (f64s)
+      k_point_update<double, double><<<blocks, 128, 0, st>>>(static_cast<double*>(S), static_cast<double*>(T), d_pts,
+                                                             d_delta, npts, d_cum, d_len, d, R, k, precision, stats);
+    else
+      k_point_update<double, float><<<blocks, 128, 0, st>>>(static_cast<float*>(S), static_cast<double*>(T), d_pts,
+                                                            d_delta, npts, d_cum, d_len, d, R, k, precision, stats);
+  } else {
+    if (f64s)
+      k_point_update<float, double><<<blocks, 128, 0, st>>>(static_cast<double*>(S), static_cast<float*>(T), d_pts,
+                                                            d_delta, npts, d_cum, d_len, d, R, k, precision, stats);
+    else
+      k_point_update<float, float><<<blocks, 128, 0, st>>>(static_cast<float*>(S), static_cast<float*>(T), d_pts,
+                                                           d_delta, npts, d_cum, d_len, d, R, k, precision, stats);
+  }
+  TSK_LAUNCH_CHECK(ctx, "k_point_update");
   return TSK_OK;
 }

@@ -531,3 +531,12 @@ def test_point_update_equals_sketching_the_updated_series_with_the_build_normali
     Rc = synth.count_sketch_R(d, k, 5)
     D = o.point_update(np.zeros((k, n)), Rc, sigma, [(4, 50, 1.0)])
     assert np.count_nonzero(D) == 1 and D[h[4], 50] == pytest.approx(sg[4] / sigma[4])
+
+
+def test_znorm_with_build_statistics_matches_scipy():
+    rng = np.random.default_rng(47)
+    T = np.cumsum(rng.normal(size=(4, 90)), axis=1)
+    T[2] = 3.0                                            # sigma = 0 stream
+    out = o.znorm_with(T, T.mean(axis=1), T.std(axis=1))
+    np.testing.assert_allclose(out[[0, 1, 3]], scipy.stats.zscore(T[[0, 1, 3]], axis=1, ddof=0), rtol=1e-12, atol=1e-12)
+    assert np.all(out[2] == 0.0)
