@@ -43,6 +43,7 @@
 #include <cfloat>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 namespace {
 
@@ -342,10 +343,66 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
   const int dA = d0 + lane * kVh;  // first diagonal of half a (half b: + kHalf)
   const float2 kMinusOne2 = make_float2(-1.f, -1.f);
 
-  // ---- exact anchors c(r0, r0 + dA + v) and c(r0, r0 + dA + 256 + v) in float64:
-  //      sum_t (x[r0+t] - mean_r0) * x[c + t]
+  // ---- anchors c(r0, r0 + dA + v) and c(r0, r0 + dA + 256 + v) at the first row
   float2 cov2[kVh];
-  {
+  if constexpr (std::is_same<TX, float>::value) {
+    // float32, from centred values: the row window a_t = x[r0+t] - mean_r0 (two-term
+    // mean), the column samples shifted by a nearby sample ref (one subtraction per
+    // loaded sample), then c = sum_t a_t (x[c+t] - ref) - (mean_c - ref) sum_t a_t,
+    // exact algebra on the rounded a_t.  Every term is of the size of the windows'
+    // spread, so the float32 sums carry ~1e-7 relative error per term and no
+    // cancellation of the series' offset.
+    const int baseA = r0 + dA, baseB = baseA + kHalf;
+    const double mr = a.wa.mu[wb + r0];
+    const float mrh = static_cast<float>(mr), mrl = static_cast<float>(mr - static_cast<double>(mrh));
+    const float refA = baseA < nc ? xc[baseA] : 0.f;
+    const float refB = baseB < nc ? xc[baseB] : 0.f;
+    float accA[kVh], accB[kVh], wa_[kVh], wbv[kVh];
+#pragma unroll
+    for (int v = 0; v < kVh; ++v) {
+      accA[v] = 0.f;
+      accB[v] = 0.f;
+      wa_[v] = (baseA + v < nc) ? __fsub_rn(xc[baseA + v], refA) : 0.f;
+      wbv[v] = (baseB + v < nc) ? __fsub_rn(xc[baseB + v], refB) : 0.f;
+    }
+    float sa = 0.f;
+    int t0 = 0;
+    for (; t0 + kVh <= m; t0 += kVh) {
+#pragma unroll
+      for (int u = 0; u < kVh; ++u) {
+        const float at = __fsub_rn(__fsub_rn(x[r0 + t0 + u], mrh), mrl);
+        sa = __fadd_rn(sa, at);
+#pragma unroll
+        for (int v = 0; v < kVh; ++v) {
+          accA[v] = __fmaf_rn(at, wa_[(v + u) & (kVh - 1)], accA[v]);
+          accB[v] = __fmaf_rn(at, wbv[(v + u) & (kVh - 1)], accB[v]);
+        }
+        const int ia = baseA + t0 + u + kVh, ib = baseB + t0 + u + kVh;
+        wa_[u] = ia < nc ? __fsub_rn(xc[ia], refA) : 0.f;
+        wbv[u] = ib < nc ? __fsub_rn(xc[ib], refB) : 0.f;
+      }
+    }
+    for (int t = t0; t < m; ++t) {
+      const float at = __fsub_rn(__fsub_rn(x[r0 + t], mrh), mrl);
+      sa = __fadd_rn(sa, at);
+#pragma unroll
+      for (int v = 0; v < kVh; ++v) {
+        const int ia = baseA + v + t, ib = baseB + v + t;
+        accA[v] = __fmaf_rn(at, ia < nc ? __fsub_rn(xc[ia], refA) : 0.f, accA[v]);
+        accB[v] = __fmaf_rn(at, ib < nc ? __fsub_rn(xc[ib], refB) : 0.f, accB[v]);
+      }
+    }
+    const double* muc = a.wa.mu + wbc;
+#pragma unroll
+    for (int v = 0; v < kVh; ++v) {
+      const float ca = static_cast<float>(static_cast<double>(accA[v]) -
+                                         (muc[baseA + v] - static_cast<double>(refA)) * static_cast<double>(sa));
+      const float cb = static_cast<float>(static_cast<double>(accB[v]) -
+                                         (muc[baseB + v] - static_cast<double>(refB)) * static_cast<double>(sa));
+      cov2[v] = make_float2(ca, cb);
+    }
+  } else {
+    // float64 samples: the anchors in float64, sum_t (x[r0+t] - mean_r0) * x[c + t]
     double accA[kVh], accB[kVh], wa_[kVh], wbv[kVh];
     const int baseA = r0 + dA, baseB = baseA + kHalf;
 #pragma unroll
