@@ -514,56 +514,70 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
     ering = (ering + kVh == kRingEntries) ? 0 : ering + kVh;
     float2* rowp = &w.rowbuf[sb][0];
     const int lx = lane ^ (sb & 8);  // row-buffer swizzle: lane ^ (step & 15) = lx ^ sr
+    // keys of one row (slot c = (v + sr) % 8 holds the column of diagonal v), with
+    // the covariance advanced to the next row
+    auto row_keys = [&](int sr, int i, float2 rdf2, float2 rdg2, float2 rinv2, float (&kA)[kVh],
+                        float (&kB)[kVh]) {
+#pragma unroll
+      for (int v = 0; v < kVh; ++v) {
+        const int c = (v + sr) & (kVh - 1);
+        const float2 t = __fmul2_rn(cov2[v], cinv2[c]);
+        const float2 r = __ffma2_rn(t, rinv2, kMinusOne2);  // rho - 1: full relative precision near rho = 1
+        float ka = tag_key(r.x, tagv[v]);
+        float kb = tag_key(r.y, tagv[v]);
+        if (MASKED) {
+          const bool rowok = i < rEnd;
+          ka = (rowok && i + dA + v < l) ? ka : kEmpty;
+          kb = (rowok && i + dA + kHalf + v < l) ? kb : kEmpty;
+        }
+        kA[v] = ka;
+        kB[v] = kb;
+        cov2[v] = __ffma2_rn(rdf2, cdg2[c], cov2[v]);
+        cov2[v] = __ffma2_rn(cdf2[c], rdg2, cov2[v]);
+      }
+      const float rka = fmaxf(max3f(max3f(max3f(kA[0], kA[1], kA[2]), kA[3], kA[4]), kA[5], kA[6]), kA[7]);
+      const float rkb = fmaxf(max3f(max3f(max3f(kB[0], kB[1], kB[2]), kB[3], kB[4]), kB[5], kB[6]), kB[7]);
+      rowp[sr * 32 + (lx ^ sr)] = make_float2(rka, rkb);
+    };
+    // the column in slot c0 leaves the lane (to lane - 1; lane 0's is complete for
+    // this band) and the column entering from the ring takes its place
+    auto exit_column = [&](int sr, int s, float la, float lb) {
+      const float ia = __shfl_down_sync(TSK_FULL_MASK, la, 1);
+      const float ib = __shfl_down_sync(TSK_FULL_MASK, lb, 1);
+      if (lane == 0) w.colbuf[s] = make_float2(la, lb);
+      ckA[sr] = (lane == 31) ? kEmpty : ia;
+      ckB[sr] = (lane == 31) ? kEmpty : ib;
+      const int o = sr ^ rx;
+      cdf2[sr] = ringb[o];
+      cdg2[sr] = ringb[kRingEntries + o];
+      cinv2[sr] = ringb[2 * kRingEntries + o];
+    };
 #pragma unroll
     for (int gg = 0; gg < kVh / 2; ++gg) {
       const int g = sb / 2 + gg;
       const float4 rf4 = w.rrow[buf][0][g], rg4 = w.rrow[buf][1][g], ri4 = w.rrow[buf][2][g];
+      // rows s0 = 2gg and s0 + 1 of the 8-row block; column maxima are folded over
+      // the two rows with 3-input max: slot c takes the key of diagonal (c - s0) % 8
+      // of row s0 and of diagonal (c - s0 - 1) % 8 of row s0 + 1
+      const int s0 = 2 * gg;
+      const int i0 = r0 + S0 + sb + s0;
+      float k0A[kVh], k0B[kVh], k1A[kVh], k1B[kVh];
+      row_keys(s0, i0, make_float2(rf4.x, rf4.y), make_float2(rg4.x, rg4.y), make_float2(ri4.x, ri4.y), k0A, k0B);
+      // slot s0 leaves after row s0: its last key is diagonal 0 of row s0
+      exit_column(s0, sb + s0, fmaxf(ckA[s0], k0A[0]), fmaxf(ckB[s0], k0B[0]));
+      row_keys(s0 + 1, i0 + 1, make_float2(rf4.z, rf4.w), make_float2(rg4.z, rg4.w), make_float2(ri4.z, ri4.w),
+               k1A, k1B);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int sr = 2 * gg + h;   // step within the 8-row block (compile-time)
-        const int s = sb + sr;       // step within the chunk
-        const int i = r0 + S0 + s;
-        const float2 rdf2 = h ? make_float2(rf4.z, rf4.w) : make_float2(rf4.x, rf4.y);
-        const float2 rdg2 = h ? make_float2(rg4.z, rg4.w) : make_float2(rg4.x, rg4.y);
-        const float2 rinv2 = h ? make_float2(ri4.z, ri4.w) : make_float2(ri4.x, ri4.y);
-        float kA[kVh], kB[kVh];
-#pragma unroll
-        for (int v = 0; v < kVh; ++v) {
-          const int c = (v + sr) & (kVh - 1);
-          const float2 t = __fmul2_rn(cov2[v], cinv2[c]);
-          const float2 r = __ffma2_rn(t, rinv2, kMinusOne2);  // rho - 1: full relative precision near rho = 1
-          float ka = tag_key(r.x, tagv[v]);
-          float kb = tag_key(r.y, tagv[v]);
-          if (MASKED) {
-            const bool rowok = i < rEnd;
-            ka = (rowok && i + dA + v < l) ? ka : kEmpty;
-            kb = (rowok && i + dA + kHalf + v < l) ? kb : kEmpty;
-          }
-          kA[v] = ka;
-          kB[v] = kb;
-          ckA[c] = fmaxf(ckA[c], ka);
-          ckB[c] = fmaxf(ckB[c], kb);
-          cov2[v] = __ffma2_rn(rdf2, cdg2[c], cov2[v]);
-          cov2[v] = __ffma2_rn(cdf2[c], rdg2, cov2[v]);
-        }
-        const float rka = fmaxf(max3f(max3f(max3f(kA[0], kA[1], kA[2]), kA[3], kA[4]), kA[5], kA[6]), kA[7]);
-        const float rkb = fmaxf(max3f(max3f(max3f(kB[0], kB[1], kB[2]), kB[3], kB[4]), kB[5], kB[6]), kB[7]);
-        rowp[sr * 32 + (lx ^ sr)] = make_float2(rka, rkb);
-        // the columns in slot s % 8 (diagonal offset 0 of this lane) leave the lane
-        const int c0 = sr;
-        const float la = ckA[c0], lb = ckB[c0];
-        const float ia = __shfl_down_sync(TSK_FULL_MASK, la, 1);
-        const float ib = __shfl_down_sync(TSK_FULL_MASK, lb, 1);
-        if (lane == 0) w.colbuf[s] = make_float2(la, lb);
-        ckA[c0] = (lane == 31) ? kEmpty : ia;
-        ckB[c0] = (lane == 31) ? kEmpty : ib;
-        {
-          const int o = sr ^ rx;
-          cdf2[c0] = ringb[o];
-          cdg2[c0] = ringb[kRingEntries + o];
-          cinv2[c0] = ringb[2 * kRingEntries + o];
+      for (int c = 0; c < kVh; ++c) {
+        if (c == s0) {  // the column that entered after row s0 has only row s0 + 1's key (diagonal 7)
+          ckA[c] = fmaxf(ckA[c], k1A[kVh - 1]);
+          ckB[c] = fmaxf(ckB[c], k1B[kVh - 1]);
+        } else {
+          ckA[c] = max3f(ckA[c], k0A[(c - s0) & (kVh - 1)], k1A[(c - s0 - 1) & (kVh - 1)]);
+          ckB[c] = max3f(ckB[c], k0B[(c - s0) & (kVh - 1)], k1B[(c - s0 - 1) & (kVh - 1)]);
         }
       }
+      exit_column(s0 + 1, sb + s0 + 1, ckA[s0 + 1], ckB[s0 + 1]);
     }
     }
     flush_chunk(w, kChunk, r0 + S0, d0, l, best, bestc, lane);
