@@ -55,7 +55,7 @@ constexpr int kRingEntries = 384;        // column ring entries of (half a, half
 constexpr int kRingInit = 288;           // entries filled before the first row
 constexpr int kWarps = 4;                // warps per CTA
 constexpr int kMaxClaim = 16;            // work units a warp claims at once (at most)
-constexpr int kMaxWalk = 16384;          // rows walked from one float64 anchor (at most)
+constexpr int kMaxWalk = 8192;           // rows walked from one anchor (at most)
 constexpr int kWinChunk = 1024;          // windows per window-stats CTA
 constexpr int kWinThreads = 256;
 constexpr int kPad = 2048;               // zeroed slack after each stream's window arrays

@@ -7,8 +7,8 @@ float32 recurrence guarantees:
   P_ref <= P_gpu <= sqrt(P_ref^2 + 4 m DELTA32).
 The float32 path reports the exact distance of the neighbour it chose, and it
 chooses among correlations computed to within DELTA32 = 1.5e-5 (each recurrence
-step rounds the running covariance: sqrt(2 * 16384 steps) * 2^-24 ~ 1.1e-5 over
-the longest walk between float64 anchors), so the chosen neighbour's true rho
+step rounds the running covariance: sqrt(2 * 8192 steps) * 2^-24 ~ 7.6e-6 over
+the longest walk between anchors, with margin), so the chosen neighbour's true rho
 is within 2 DELTA32 of the best and dist^2 = 2m(1 - rho) is within 4m DELTA32
 of the minimum.  The relative bar is the binding one unless P_ref is below
 about 0.04 sqrt(2m) (close matches, 1 - rho < ~1e-3).  The floor covers exact
