@@ -17,8 +17,9 @@
 //                   shared memory shifted by its first sample; window means and
 //                   norms come from float-float prefix sums (no float64 on the
 //                   hot path: the FP64 pipe runs at 1/64 of FP32); each thread
-//                   forms 8 consecutive sliding dot products with the centred
-//                   query in float32 (32 FMAs per vector load, padded staging so
+//                   forms 8 consecutive sliding dot products with two centred
+//                   queries at a time in paired float32 FMAs (64 FMAs in 32
+//                   issue slots per vector load of samples; swizzled staging so
 //                   the loads are free of bank conflicts).  The largest key
 //                   rho - 1 and lowest window index merge per (series,
 //                   discord, stream) in a packed 64-bit word with atomicMax.
@@ -98,9 +99,11 @@ __device__ __forceinline__ FF ff_shfl(FF v, int lane) {
   return {__shfl_sync(TSK_FULL_MASK, v.h, lane), __shfl_sync(TSK_FULL_MASK, v.l, lane)};
 }
 
-// padded staging index: 4 spare floats after every 32, so that lanes reading
-// float4s 32 bytes apart fall in distinct bank groups
-__device__ __forceinline__ int xs_phys(int p) { return p + ((p >> 5) << 2); }
+// staging index: 16-byte granule g goes to g ^ ((g >> 3) & 1), so that the 8
+// lanes of a quarter warp reading float4s 32 bytes apart (samples 8 l + c, any
+// c = 0 mod 4) fall in 8 distinct bank groups, and 32 consecutive scalar stores
+// stay a permutation of one 128-byte row
+__device__ __forceinline__ int xs_phys(int p) { return p ^ (((p >> 5) & 1) << 2); }
 
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 
@@ -156,25 +159,77 @@ __global__ void __launch_bounds__(256) k_dd_query(const TX* __restrict__ T, DimA
                                q_const ? 1.f : 0.f);
 }
 
+// Sliding dot products of the centred queries with the 8 consecutive windows
+// starting at staged sample w0.  One query (qs contiguous): 32 FMAs per 16-byte
+// load of samples.  Two queries (qs interleaved, qs[2k + q]): paired FFMA2 with
+// (sample, sample) x (q0_k, q1_k), 64 FMAs in 32 issue slots per load.
+template <int NQ>
+__device__ __forceinline__ void dot_windows(const float* __restrict__ xs, const float* __restrict__ qs, int m4,
+                                            int w0, float (&acc)[2][kWinPerThread]) {
+  float4 A = *reinterpret_cast<const float4*>(xs + xs_phys(w0));
+  float4 B = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + 4));
+  if constexpr (NQ == 1) {
+#pragma unroll
+    for (int u = 0; u < kWinPerThread; ++u) acc[0][u] = 0.f;
+    for (int kk = 0; kk < m4; kk += 4) {
+      const float4 C = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + kk + 8));
+      const float v[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+      const float4 qv = *reinterpret_cast<const float4*>(qs + kk);
+#pragma unroll
+      for (int u = 0; u < kWinPerThread; ++u) {
+        acc[0][u] = __fmaf_rn(qv.x, v[u + 0], acc[0][u]);
+        acc[0][u] = __fmaf_rn(qv.y, v[u + 1], acc[0][u]);
+        acc[0][u] = __fmaf_rn(qv.z, v[u + 2], acc[0][u]);
+        acc[0][u] = __fmaf_rn(qv.w, v[u + 3], acc[0][u]);
+      }
+      A = B;
+      B = C;
+    }
+  } else {
+    float2 acc2[kWinPerThread];
+#pragma unroll
+    for (int u = 0; u < kWinPerThread; ++u) acc2[u] = make_float2(0.f, 0.f);
+    for (int kk = 0; kk < m4; kk += 4) {
+      const float4 C = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + kk + 8));
+      const float v[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+      const float4 q01 = *reinterpret_cast<const float4*>(qs + 2 * kk);      // (q0, q1) at kk, kk + 1
+      const float4 q23 = *reinterpret_cast<const float4*>(qs + 2 * kk + 4);  // (q0, q1) at kk + 2, kk + 3
+      const float2 qk[4] = {make_float2(q01.x, q01.y), make_float2(q01.z, q01.w), make_float2(q23.x, q23.y),
+                            make_float2(q23.z, q23.w)};
+#pragma unroll
+      for (int u = 0; u < kWinPerThread; ++u)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc2[u] = __ffma2_rn(make_float2(v[u + k], v[u + k]), qk[k], acc2[u]);
+      A = B;
+      B = C;
+    }
+#pragma unroll
+    for (int u = 0; u < kWinPerThread; ++u) {
+      acc[0][u] = acc2[u].x;
+      acc[1][u] = acc2[u].y;
+    }
+  }
+}
+
 // One CTA per (series, stream, chunk of 2048 windows), for every discord whose
 // group holds the stream.  See the file comment.
 template <typename TX>
-__global__ void __launch_bounds__(kScanThreads) k_dd_scan(const TX* __restrict__ T, DimArgs a, int64_t total_items) {
+__global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restrict__ T, DimArgs a, int64_t total_items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
   const int m4 = a.m4;
   const int ns_max = kTW + m4 + 8;                             // staged samples (zero padded)
   float* xs = reinterpret_cast<float*>(smem_raw);              // [xs_phys(ns_max)]
-  const int xs_words = xs_phys(ns_max) + 4;
-  float* qs = xs + xs_words;                                   // [m4]
-  float* w_inv = qs + m4;                                      // [kTW] 1/||window - mean|| (0: constant)
+  const int xs_words = ns_max + 8;
+  float* qs = xs + xs_words;                                   // [2 * m4] one query, or two interleaved
+  float* w_inv = qs + 2 * m4;                                  // [kTW] 1/||window - mean|| (0: constant)
   float* w_mean = w_inv + kTW;                                 // [kTW] window mean of the shifted samples
   float* p1h = w_mean + kTW;                                   // [kTW + m] prefix of shifted samples (float-float)
   float* p1l = p1h + (kTW + m);
   float* p2h = p1l + (kTW + m);                                // [kTW + m] prefix of their squares
   float* p2l = p2h + (kTW + m);
   __shared__ float segs[4][kScanThreads];
-  __shared__ unsigned long long wbest[kScanThreads / 32];
+  __shared__ unsigned long long wbest[2][kScanThreads / 32];
   const int tid = threadIdx.x;
 
   for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
@@ -286,66 +341,85 @@ __global__ void __launch_bounds__(kScanThreads) k_dd_scan(const TX* __restrict__
     }
     __syncthreads();
 
-    // ---- every discord whose group holds this stream ----
-    for (int r = 0; r < a.K; ++r) {
+    // ---- the discords whose group holds this stream, two per pass over the chunk ----
+    auto active = [&](int r) {
       const int64_t sr = static_cast<int64_t>(s) * a.K + r;
-      const float4 qi = a.qinfo[sr * a.d + j];
-      if (qi.z == 0.f) continue;
+      if (a.qinfo[sr * a.d + j].z == 0.f) return false;
       const int i_star = a.idx[sr];
-      if (t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl) continue;
-      const float* qg = a.Q + (sr * a.d + j) * m4;
-      for (int t = tid; t < m4; t += kScanThreads) qs[t] = qg[t];
+      return !(t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl);
+    };
+    // this thread's 8 windows: statistics once per item (vector loads)
+    const int w0 = tid * kWinPerThread;
+    float winv[kWinPerThread], wmean[kWinPerThread];
+    {
+      const float4 i0 = *reinterpret_cast<const float4*>(w_inv + w0);
+      const float4 i1 = *reinterpret_cast<const float4*>(w_inv + w0 + 4);
+      const float4 m0 = *reinterpret_cast<const float4*>(w_mean + w0);
+      const float4 m1 = *reinterpret_cast<const float4*>(w_mean + w0 + 4);
+      winv[0] = i0.x; winv[1] = i0.y; winv[2] = i0.z; winv[3] = i0.w;
+      winv[4] = i1.x; winv[5] = i1.y; winv[6] = i1.z; winv[7] = i1.w;
+      wmean[0] = m0.x; wmean[1] = m0.y; wmean[2] = m0.z; wmean[3] = m0.w;
+      wmean[4] = m1.x; wmean[5] = m1.y; wmean[6] = m1.z; wmean[7] = m1.w;
+    }
+    int r = 0;
+    for (;;) {
+      int ra = -1, rb = -1;
+      for (; r < a.K && ra < 0; ++r)
+        if (active(r)) ra = r;
+      if (ra < 0) break;
+      for (; r < a.K && rb < 0; ++r)
+        if (active(r)) rb = r;
+      const int nq = rb >= 0 ? 2 : 1;
+      if (nq == 1) {  // one query, contiguous
+        const float* qg = a.Q + ((static_cast<int64_t>(s) * a.K + ra) * a.d + j) * m4;
+        for (int t = tid; t < m4; t += kScanThreads) qs[t] = qg[t];
+      } else {        // two queries, interleaved (q0_k, q1_k)
+        const float* qa = a.Q + ((static_cast<int64_t>(s) * a.K + ra) * a.d + j) * m4;
+        const float* qb = a.Q + ((static_cast<int64_t>(s) * a.K + rb) * a.d + j) * m4;
+        for (int t = tid; t < m4; t += kScanThreads) *reinterpret_cast<float2*>(qs + 2 * t) = make_float2(qa[t], qb[t]);
+      }
       __syncthreads();
-      const int w0 = tid * kWinPerThread;
-      float acc[kWinPerThread];
+      float acc[2][kWinPerThread];
+      if (nq == 2)
+        dot_windows<2>(xs, qs, m4, w0, acc);
+      else
+        dot_windows<1>(xs, qs, m4, w0, acc);
 #pragma unroll
-      for (int u = 0; u < kWinPerThread; ++u) acc[u] = 0.f;
-      if (qi.w == 0.f) {  // dot products with the centred query (a constant query needs none)
-        float4 A = *reinterpret_cast<const float4*>(xs + xs_phys(w0));
-        float4 B = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + 4));
-        const float4* qs4 = reinterpret_cast<const float4*>(qs);
-        for (int kk = 0; kk < m4; kk += 4) {
-          const float4 C = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + kk + 8));
-          const float4 q = qs4[kk >> 2];
-          const float v[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+      for (int q = 0; q < 2; ++q) {
+        if (q < nq) {
+          const int64_t sr = static_cast<int64_t>(s) * a.K + (q == 0 ? ra : rb);
+          const float4 qi = a.qinfo[sr * a.d + j];
+          const int i_star = a.idx[sr];
+          unsigned long long best = 0ull;
 #pragma unroll
           for (int u = 0; u < kWinPerThread; ++u) {
-            acc[u] = __fmaf_rn(q.x, v[u + 0], acc[u]);
-            acc[u] = __fmaf_rn(q.y, v[u + 1], acc[u]);
-            acc[u] = __fmaf_rn(q.z, v[u + 2], acc[u]);
-            acc[u] = __fmaf_rn(q.w, v[u + 3], acc[u]);
+            const int w = w0 + u;
+            const int t = t0 + w;
+            if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
+            const float inv_t = winv[u];
+            float key;
+            if (qi.w != 0.f) key = (inv_t == 0.f) ? 0.0f : -0.5f;  // rho 1 (dist 0) to a constant window, else 1/2
+            else if (inv_t == 0.f) key = -0.5f;                     // rho 1/2: 2m(1 - 1/2) = m
+            else {
+              const float cov = __fmaf_rn(-wmean[u], qi.y, acc[q][u]);
+              key = fminf(0.0f, fmaxf(-2.0f, __fmaf_rn(cov * qi.x, inv_t, -1.0f)));  // rho - 1
+            }
+            best = umax64(best, tsk_pack(key, t));
           }
-          A = B;
-          B = C;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
+          if ((tid & 31) == 0) wbest[q][tid >> 5] = best;
         }
       }
-      unsigned long long best = 0ull;
-#pragma unroll
-      for (int u = 0; u < kWinPerThread; ++u) {
-        const int w = w0 + u;
-        const int t = t0 + w;
-        if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
-        const float inv_t = w_inv[w];
-        float key;
-        if (qi.w != 0.f) key = (inv_t == 0.f) ? 0.0f : -0.5f;  // rho 1 (dist 0) to a constant window, else 1/2
-        else if (inv_t == 0.f) key = -0.5f;                     // rho 1/2: 2m(1 - 1/2) = m
-        else {
-          const float cov = __fmaf_rn(-w_mean[w], qi.y, acc[u]);
-          key = fminf(0.0f, fmaxf(-2.0f, __fmaf_rn(cov * qi.x, inv_t, -1.0f)));  // rho - 1
-        }
-        best = umax64(best, tsk_pack(key, t));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
-      if ((tid & 31) == 0) wbest[tid >> 5] = best;
       __syncthreads();
-      if (tid == 0) {
+      if (tid < nq) {
         unsigned long long b = 0ull;
 #pragma unroll
-        for (int q = 0; q < kScanThreads / 32; ++q) b = umax64(b, wbest[q]);
+        for (int w = 0; w < kScanThreads / 32; ++w) b = umax64(b, wbest[tid][w]);
+        const int64_t sr = static_cast<int64_t>(s) * a.K + (tid == 0 ? ra : rb);
         if (b) atomicMax(&a.best[sr * a.d + j], b);
       }
-      __syncthreads();  // qs and wbest are reused by the next discord
+      __syncthreads();  // qs and wbest are reused by the next pass
     }
   }
 }
@@ -458,8 +532,9 @@ __global__ void k_dd_gather(const TX* __restrict__ T, const int64_t* __restrict_
 size_t scan_smem_bytes(int m) {
   const int m4 = (m + 3) & ~3;
   const int ns_max = kTW + m4 + 8;
-  const size_t xs_words = static_cast<size_t>(ns_max + ((ns_max >> 5) << 2)) + 4;
-  return (xs_words + m4 + 2 * static_cast<size_t>(kTW) + 4 * static_cast<size_t>(kTW + m)) * sizeof(float);
+  const size_t xs_words = static_cast<size_t>(ns_max) + 8;
+  return (xs_words + 2 * static_cast<size_t>(m4) + 2 * static_cast<size_t>(kTW) + 4 * static_cast<size_t>(kTW + m)) *
+         sizeof(float);
 }
 
 template <typename TX>
