@@ -129,7 +129,7 @@ TSK_API tsk_status tsk_profile_read(tsk_ctx* ctx, int32_t kernel, double* total_
  *   S      : output sketch, batch layout with k streams; float32, or float64
  *            when precision == TSK_SKETCH_FP64.
  *   stats  : output float64 [n_series][d][2] = {mu, sigma}; may be NULL.
- * Requires n_series >= 1, d >= 1, 1 <= k <= 64, every len >= 1.
+ * Requires n_series >= 1, d >= 1, 1 <= k <= 4096, every len >= 1.
  */
 TSK_API tsk_status ts_sketch_build(tsk_ctx* ctx, const void* T, int32_t t_dtype, int32_t n_series,
                                    const int32_t* series_len_host, int32_t d, const float* R, int32_t k,

@@ -580,19 +580,22 @@ extern "C" TSK_API tsk_status ts_sketch_build(tsk_ctx* ctx, const void* T, int32
   if (t_dtype != TSK_F32 && t_dtype != TSK_F64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_build: bad t_dtype");
   if (precision < TSK_SKETCH_BF16 || precision > TSK_SKETCH_FP64)
     return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_build: bad precision");
-  if (n_series < 1 || d < 1 || k < 1 || k > 64)
-    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_build: need n_series >= 1, d >= 1, 1 <= k <= 64");
+  if (n_series < 1 || d < 1 || k < 1 || k > 4096)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_build: need n_series >= 1, d >= 1, 1 <= k <= 4096");
   if ((st = check_lens(ctx, n_series, series_len_host, 1, "ts_sketch_build"))) return st;
   BatchLayout L{};
   if ((st = batch_layout(ctx, n_series, series_len_host, d, &L))) return st;
-  double* stv = stats;
-  if (!stv) {
-    if ((st = tsk_ws_require(ctx, tsk_carver::bytes_for(static_cast<size_t>(n_series) * d * 2, 8)))) return st;
-    stv = static_cast<double*>(ctx->ws);
-  }
+  const size_t stat_bytes = stats ? 0 : tsk_carver::bytes_for(static_cast<size_t>(n_series) * d * 2, 8);
+  const size_t sk_bytes = precision == TSK_SKETCH_BF16
+                              ? tsk_sketch_ws_bytes(n_series, d, k, L.total_blocks, L.total_samples, ctx->sm_count)
+                              : 0;
+  if ((st = tsk_ws_require(ctx, stat_bytes + sk_bytes))) return st;
+  tsk_carver cv(ctx->ws);
+  double* stv = stats ? stats : cv.take<double>(static_cast<size_t>(n_series) * d * 2);
+  char* skws = cv.take<char>(sk_bytes > 0 ? sk_bytes : 1);
   if ((st = tsk_launch_colstats(ctx, T, t_dtype, L.soff, L.slen, static_cast<int64_t>(n_series) * d, stv))) return st;
   return tsk_launch_sketch(ctx, T, t_dtype, n_series, L.cum, L.len, L.blk_prefix, L.total_blocks, d, R, k, precision,
-                           stv, S, 0);
+                           stv, S, L.total_samples, skws);
 }
 
 extern "C" TSK_API tsk_status ts_sketch_update_dims(tsk_ctx* ctx, void* S, const void* T_dims, int32_t t_dtype,
@@ -605,8 +608,8 @@ extern "C" TSK_API tsk_status ts_sketch_update_dims(tsk_ctx* ctx, void* S, const
     return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_update_dims: S, T_dims, R_rows_host, op_host must be non-NULL");
   if (t_dtype != TSK_F32 && t_dtype != TSK_F64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "bad t_dtype");
   if (precision < TSK_SKETCH_BF16 || precision > TSK_SKETCH_FP64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "bad precision");
-  if (n_series < 1 || nd < 1 || k < 1 || k > 64)
-    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_update_dims: need n_series >= 1, nd >= 1, 1 <= k <= 64");
+  if (n_series < 1 || nd < 1 || k < 1 || k > 4096)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_update_dims: need n_series >= 1, nd >= 1, 1 <= k <= 4096");
   for (int q = 0; q < nd; ++q)
     if (op_host[q] != 1 && op_host[q] != -1)
       return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "ts_sketch_update_dims: op[%d] must be +1 or -1", q);
@@ -829,8 +832,8 @@ extern "C" TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, con
   if (!dscore || !idx || !grp || !nn || !T || !stats || !R || !S || !dT || !dR)
     return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_backward: array arguments must be non-NULL");
   if (t_dtype != TSK_F32 && t_dtype != TSK_F64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_backward: bad t_dtype");
-  if (n_series < 1 || K < 1 || d < 1 || k < 1 || k > 64 || m < 2)
-    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_backward: need n_series, K, d >= 1, 1 <= k <= 64, m >= 2");
+  if (n_series < 1 || K < 1 || d < 1 || k < 1 || k > 4096 || m < 2)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_backward: need n_series, K, d >= 1, 1 <= k <= 4096, m >= 2");
   if ((st = check_lens(ctx, n_series, series_len_host, m, "mp_backward"))) return st;
   BatchLayout L{};
   if ((st = batch_layout(ctx, n_series, series_len_host, d, &L))) return st;

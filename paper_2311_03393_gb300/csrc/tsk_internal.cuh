@@ -181,7 +181,10 @@ tsk_status tsk_launch_colstats(tsk_ctx* ctx, const void* T, int t_dtype, const i
 tsk_status tsk_launch_sketch(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_series, const int64_t* d_cum,
                              const int32_t* d_len, const int64_t* d_blk_prefix, int64_t total_blocks, int32_t d,
                              const float* R, int32_t k, int32_t precision, const double* stats, void* S,
-                             int64_t max_len);
+                             int64_t total_samples, char* ws);
+// Workspace of tsk_launch_sketch (bfloat16 precision: R in bf16, per-stream constants, partial sums).
+size_t tsk_sketch_ws_bytes(int32_t n_series, int32_t d, int32_t k, int64_t total_blocks, int64_t total_samples,
+                           int sm_count);
 tsk_status tsk_launch_update_dims(tsk_ctx* ctx, void* S, const void* T_dims, int t_dtype, int32_t n_series,
                                   const int64_t* d_cum, const int32_t* d_len, int64_t total_samples, int32_t nd,
                                   const float* d_Rrows, const int8_t* d_op, int32_t k, int32_t precision,

@@ -6,8 +6,11 @@
 // in float64, rounded to bfloat16 (nearest even) and fed to the tensor cores;
 // products are summed in float32.
 #include "tsk_internal.cuh"
+#include "tsk_ff.cuh"
 
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 namespace {
 
@@ -15,7 +18,10 @@ constexpr int kStatThreads = 256;
 
 // ---------------------------------------------------------------------------
 // Column statistics: mean and population std of every stream, float64.
-// Sums are taken of x - x[0] (a shift that keeps them well conditioned).
+// Sums are taken of x - x[0] (a shift that keeps them well conditioned).  For
+// float32 series they are accumulated in float-float (the shift is exact as a
+// two-sum, squares as product plus fma error), ~2^-44 relative, so the FP64
+// pipe is used only for the final combination.
 // ---------------------------------------------------------------------------
 template <typename TIn>
 __global__ void __launch_bounds__(kStatThreads) k_colstats(const TIn* __restrict__ T, const int64_t* __restrict__ off,
@@ -27,12 +33,26 @@ __global__ void __launch_bounds__(kStatThreads) k_colstats(const TIn* __restrict
   const double x0 = tsk_ld(T, base);
   double s1 = 0.0, s2 = 0.0;
   bool bad = false;
-  for (int t = threadIdx.x; t < n; t += kStatThreads) {
-    const double x = tsk_ld(T, base + t);
-    bad |= !isfinite(x);
-    const double y = x - x0;
-    s1 += y;
-    s2 = fma(y, y, s2);
+  if constexpr (std::is_same<TIn, float>::value) {
+    const float xf0 = T[base];
+    FF a1{0.f, 0.f}, a2{0.f, 0.f};
+    for (int t = threadIdx.x; t < n; t += kStatThreads) {
+      const float x = T[base + t];
+      bad |= !isfinite(x);
+      const FF y = ff_two_sum(x, -xf0);
+      a1 = ff_add(a1, y);
+      a2 = ff_add(a2, ff_sqr(y));
+    }
+    s1 = static_cast<double>(a1.h) + static_cast<double>(a1.l);
+    s2 = static_cast<double>(a2.h) + static_cast<double>(a2.l);
+  } else {
+    for (int t = threadIdx.x; t < n; t += kStatThreads) {
+      const double x = tsk_ld(T, base + t);
+      bad |= !isfinite(x);
+      const double y = x - x0;
+      s1 += y;
+      s2 = fma(y, y, s2);
+    }
   }
   if (bad) atomicOr(err, TSK_DEVERR_NONFINITE);
   __shared__ double r1[kStatThreads / 32], r2[kStatThreads / 32];
@@ -100,89 +120,135 @@ __device__ __forceinline__ uint16_t tbar_bf16(double x, const NormC& c) {
 }
 
 // ---------------------------------------------------------------------------
-// bfloat16 tensor-core sketch.  One CTA = 64 time points of one series x all
-// k outputs; 4 warps, one m16 tile each, ceil(k/8) n8 tiles; K = d in chunks
-// of 16 staged through shared memory.
+// bfloat16 tensor-core sketch.
+//
+// k_sketch_prep turns R into bfloat16 bits, transposed and zero-padded
+// (Rt[g][j], kp x dp), and the per-stream statistics into NormC constants, once
+// per call.  k_sketch_bf16: one CTA = 64 time points x 64 outputs (blockIdx.y
+// picks the group of 64 outputs) x one range of dimensions (blockIdx.z, when
+// the grid would otherwise leave SMs idle); 4 warps, one m16 tile of time
+// points each, up to 8 n8 tiles; dimensions in stages of 32, the next stage's
+// samples loaded into registers while the current stage's MMAs run.  With
+// several dimension ranges the partial sums go to a workspace and
+// k_sketch_reduce adds them in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 constexpr int kSkT = 64;       // time points per CTA
 constexpr int kSkThreads = 128;
-constexpr int kSkPad = 24;     // padded row of 16 bf16 (conflict-free fragment loads)
+constexpr int kSkKC = 32;      // dimensions per stage
+constexpr int kSkRow = kSkKC + 8;  // padded smem row (80 bytes: conflict-free fragment loads)
+
+__global__ void k_sketch_prep(const float* __restrict__ R, int32_t d, int32_t k, int32_t dp, int32_t kp,
+                              const double* __restrict__ stats, int64_t nstreams, uint16_t* __restrict__ Rt,
+                              NormC* __restrict__ nc) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nr = static_cast<int64_t>(kp) * dp;
+  if (e < nr) {
+    const int g = static_cast<int>(e / dp), j = static_cast<int>(e % dp);
+    Rt[e] = (g < k && j < d) ? tsk_f64_to_bf16_bits(static_cast<double>(R[static_cast<int64_t>(j) * k + g])) : 0;
+  }
+  if (e < nstreams) {
+    const double mu = stats[2 * e], sg = stats[2 * e + 1];
+    nc[e] = make_normc(mu, sg > 0.0 ? 1.0 / sg : 0.0);
+  }
+}
 
 template <typename TIn>
 __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restrict__ T, const int64_t* __restrict__ cum,
                                                            const int32_t* __restrict__ len,
                                                            const int64_t* __restrict__ blk_prefix, int32_t n_series,
-                                                           int32_t d, const float* __restrict__ R, int32_t k,
-                                                           const double* __restrict__ stats, float* __restrict__ S) {
-  __shared__ __align__(16) uint16_t As[kSkT][kSkPad];
-  __shared__ __align__(16) uint16_t Bs[64][kSkPad];
-  __shared__ NormC snc[16];
+                                                           int32_t d, int32_t dchunk, const uint16_t* __restrict__ Rt,
+                                                           int32_t dp, int32_t k, const NormC* __restrict__ nc,
+                                                           float* __restrict__ S, int64_t part_stride) {
+  __shared__ __align__(16) uint16_t As[kSkT][kSkRow];
+  __shared__ __align__(16) uint16_t Bs[64][kSkRow];
+  __shared__ NormC snc[kSkKC];
 
   const int s = tsk_find_segment<int64_t>(blk_prefix, n_series, static_cast<int64_t>(blockIdx.x));
   const int n = len[s];
   const int t0 = static_cast<int>(blockIdx.x - blk_prefix[s]) * kSkT;
   const int64_t tbase = static_cast<int64_t>(d) * cum[s];
-  const int64_t sbase = static_cast<int64_t>(k) * cum[s];
+  const int64_t sbase = static_cast<int64_t>(k) * cum[s] + static_cast<int64_t>(blockIdx.z) * part_stride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gid = lane >> 2, tig = lane & 3;
-  const int NT = (k + 7) >> 3;
+  const int gbase = static_cast<int>(blockIdx.y) * 64;
+  const int NT = min(8, (k - gbase + 7) >> 3);
+  const int jb = static_cast<int>(blockIdx.z) * dchunk;
+  const int je = min(d, jb + dchunk);
 
   float acc[8][4];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.f;
+  for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
 
-  for (int j0 = 0; j0 < d; j0 += 16) {
-    if (tid < 16) {
-      const int j = j0 + tid;
-      double mu = 0.0, ri = 0.0;
-      if (j < d) {
-        mu = stats[2 * (static_cast<int64_t>(s) * d + j) + 0];
-        const double sg = stats[2 * (static_cast<int64_t>(s) * d + j) + 1];
-        ri = sg > 0.0 ? 1.0 / sg : 0.0;
-      }
-      snc[tid] = make_normc(mu, ri);
-    }
-    __syncthreads();
+  // this thread's share of a stage: 16 samples (dimension e >> 6, time e & 63 for
+  // e = tid + 128 u) and two 8-wide rows of R (output e2 >> 2, dimensions 8 (e2 & 3)..)
+  TIn xv[16];
+  uint4 rv[2];
+  auto load_stage = [&](int j0) {
 #pragma unroll
-    for (int u = 0; u < (16 * kSkT) / kSkThreads; ++u) {
+    for (int u = 0; u < 16; ++u) {
       const int e = tid + u * kSkThreads;
-      const int jl = e / kSkT, tl = e % kSkT;
-      const int j = j0 + jl, t = t0 + tl;
-      uint16_t h = 0;
-      if (j < d && t < n) h = tbar_bf16(T[tbase + static_cast<int64_t>(j) * n + t], snc[jl]);
-      As[tl][jl] = h;
+      const int j = j0 + (e >> 6), t = t0 + (e & 63);
+      xv[u] = (j < je && t < n) ? T[tbase + static_cast<int64_t>(j) * n + t] : TIn(0);
     }
-    for (int e = tid; e < 16 * NT * 8; e += kSkThreads) {
-      const int g = e / 16, jl = e % 16;
-      const int j = j0 + jl;
-      uint16_t h = 0;
-      if (j < d && g < k) h = tsk_f64_to_bf16_bits(static_cast<double>(R[static_cast<int64_t>(j) * k + g]));
-      Bs[g][jl] = h;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e2 = tid + u * kSkThreads;
+      const int g = gbase + (e2 >> 2), jj = j0 + 8 * (e2 & 3);
+      rv[u] = *reinterpret_cast<const uint4*>(Rt + static_cast<int64_t>(g) * dp + jj);
+    }
+  };
+  load_stage(jb);
+  for (int j0 = jb; j0 < je; j0 += kSkKC) {
+    __syncthreads();  // the previous stage's fragments have been read
+    if (tid < kSkKC) snc[tid] = (j0 + tid < je) ? nc[static_cast<int64_t>(s) * d + j0 + tid] : make_normc(0.0, 0.0);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + u * kSkThreads;
+      const int jl = e >> 6, tl = e & 63;
+      As[tl][jl] = (j0 + jl < je && t0 + tl < n) ? tbar_bf16(xv[u], snc[jl]) : uint16_t(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e2 = tid + u * kSkThreads;
+      uint4 r = rv[u];
+      // dimensions past this range's end contribute nothing
+      const int jj = j0 + 8 * (e2 & 3);
+      if (jj + 8 > je) {
+        uint16_t* h = reinterpret_cast<uint16_t*>(&r);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (jj + q >= je) h[q] = 0;
+      }
+      *reinterpret_cast<uint4*>(&Bs[e2 >> 2][8 * (e2 & 3)]) = r;
     }
     __syncthreads();
-    const int r = warp * 16 + gid;
-    const uint32_t a0 = *reinterpret_cast<const uint32_t*>(&As[r][2 * tig]);
-    const uint32_t a1 = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * tig]);
-    const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&As[r][2 * tig + 8]);
-    const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * tig + 8]);
+    if (j0 + kSkKC < je) load_stage(j0 + kSkKC);  // overlaps the MMAs below
+    const int r0 = warp * 16 + gid;
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      if (nt < NT) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][2 * tig]);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][2 * tig + 8]);
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};\n"
-            : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    for (int ks = 0; ks < kSkKC; ks += 16) {
+      const uint32_t a0 = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * tig]);
+      const uint32_t a1 = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * tig]);
+      const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * tig + 8]);
+      const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * tig + 8]);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        if (nt < NT) {
+          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][ks + 2 * tig]);
+          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][ks + 2 * tig + 8]);
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+              : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
       }
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     if (nt < NT) {
-      const int g = nt * 8 + 2 * tig;
+      const int g = gbase + nt * 8 + 2 * tig;
       const int t = t0 + warp * 16 + gid;
       if (t < n) {
         if (g < k) S[sbase + static_cast<int64_t>(g) * n + t] = acc[nt][0];
@@ -193,6 +259,16 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restric
         if (g + 1 < k) S[sbase + static_cast<int64_t>(g + 1) * n + t + 8] = acc[nt][3];
       }
     }
+  }
+}
+
+// S = sum over the dimension ranges of the partial sketches, in range order
+__global__ void k_sketch_reduce(const float* __restrict__ part, int nparts, int64_t total, float* __restrict__ S) {
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float v = 0.f;
+    for (int q = 0; q < nparts; ++q) v += part[static_cast<int64_t>(q) * total + e];
+    S[e] = v;
   }
 }
 
@@ -332,32 +408,88 @@ tsk_status tsk_launch_colstats(tsk_ctx* ctx, const void* T, int t_dtype, const i
   return TSK_OK;
 }
 
+// Dimension ranges of the bfloat16 sketch: enough CTAs to fill the GPU about 8
+// deep, each range at least 256 dimensions.
+static void sketch_split(int64_t total_blocks, int32_t d, int32_t k, int sm_count, int* nparts, int* dchunk) {
+  const int64_t tiles = total_blocks * ((k + 63) / 64);
+  const int64_t want = static_cast<int64_t>(sm_count) * 8;
+  int p = static_cast<int>(std::min<int64_t>(std::max<int64_t>(1, (want + tiles - 1) / tiles), std::max(1, d / 256)));
+  int c = (d + p - 1) / p;
+  c = (c + kSkKC - 1) / kSkKC * kSkKC;
+  p = (d + c - 1) / c;
+  *nparts = p;
+  *dchunk = c;
+}
+
+size_t tsk_sketch_ws_bytes(int32_t n_series, int32_t d, int32_t k, int64_t total_blocks, int64_t total_samples,
+                           int sm_count) {
+  int p = 1, c = d;
+  sketch_split(total_blocks, d, k, sm_count, &p, &c);
+  const size_t dp = (static_cast<size_t>(d) + kSkKC - 1) / kSkKC * kSkKC + kSkKC;
+  const size_t kp = (static_cast<size_t>(k) + 63) / 64 * 64;
+  size_t b = tsk_carver::bytes_for(kp * dp, 2) + tsk_carver::bytes_for(static_cast<size_t>(n_series) * d, sizeof(NormC));
+  if (p > 1) b += tsk_carver::bytes_for(static_cast<size_t>(p) * k * total_samples, 4);
+  return b + 512;
+}
+
 tsk_status tsk_launch_sketch(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n_series, const int64_t* d_cum,
                              const int32_t* d_len, const int64_t* d_blk_prefix, int64_t total_blocks, int32_t d,
                              const float* R, int32_t k, int32_t precision, const double* stats, void* S,
-                             int64_t /*max_len*/) {
+                             int64_t total_samples, char* ws) {
   if (total_blocks <= 0) return TSK_OK;
   if (total_blocks > 0x7fffffff) return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "batch too large");
   const dim3 grid(static_cast<unsigned>(total_blocks));
   const bool f64in = t_dtype == TSK_F64;
-  tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
+  cudaStream_t st = ctx->stream;
   if (precision == TSK_SKETCH_BF16) {
-    if (f64in)
-      k_sketch_bf16<double><<<grid, kSkThreads, 0, ctx->stream>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
-    else
-      k_sketch_bf16<float><<<grid, kSkThreads, 0, ctx->stream>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
+    int parts = 1, dchunk = d;
+    sketch_split(total_blocks, d, k, ctx->sm_count, &parts, &dchunk);
+    // the stage loop reads R rows 8 dimensions at a time up to one stage past a range
+    const int32_t dp = (d + kSkKC - 1) / kSkKC * kSkKC + kSkKC;
+    const int32_t kp = (k + 63) / 64 * 64;
+    tsk_carver cv(ws);
+    uint16_t* Rt = cv.take<uint16_t>(static_cast<size_t>(kp) * dp);
+    NormC* nc = cv.take<NormC>(static_cast<size_t>(n_series) * d);
+    float* part = parts > 1 ? cv.take<float>(static_cast<size_t>(parts) * k * total_samples) : nullptr;
+    const int64_t nstreams = static_cast<int64_t>(n_series) * d;
+    const int64_t nprep = std::max<int64_t>(static_cast<int64_t>(kp) * dp, nstreams);
+    k_sketch_prep<<<static_cast<unsigned>((nprep + 255) / 256), 256, 0, st>>>(R, d, k, dp, kp, stats, nstreams, Rt, nc);
+    TSK_LAUNCH_CHECK(ctx, "k_sketch_prep");
+    const dim3 grid_bf16(static_cast<unsigned>(total_blocks), static_cast<unsigned>(kp / 64),
+                         static_cast<unsigned>(parts));
+    float* out = parts > 1 ? part : static_cast<float*>(S);
+    const int64_t pstride = static_cast<int64_t>(k) * total_samples;
+    {
+      tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
+      if (f64in)
+        k_sketch_bf16<double><<<grid_bf16, kSkThreads, 0, st>>>(static_cast<const double*>(T), d_cum, d_len,
+                                                                  d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc,
+                                                                  out, pstride);
+      else
+        k_sketch_bf16<float><<<grid_bf16, kSkThreads, 0, st>>>(static_cast<const float*>(T), d_cum, d_len,
+                                                                 d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc,
+                                                                 out, pstride);
+    }
     TSK_LAUNCH_CHECK(ctx, "k_sketch_bf16");
+    if (parts > 1) {
+      const int64_t total = pstride;
+      const int64_t blocks = std::min<int64_t>((total + 255) / 256, static_cast<int64_t>(ctx->sm_count) * 16);
+      k_sketch_reduce<<<static_cast<unsigned>(blocks), 256, 0, st>>>(part, parts, total, static_cast<float*>(S));
+      TSK_LAUNCH_CHECK(ctx, "k_sketch_reduce");
+    }
   } else if (precision == TSK_SKETCH_FP32) {
+    tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
     if (f64in)
-      k_sketch_fma<double, float><<<grid, 128, 0, ctx->stream>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
+      k_sketch_fma<double, float><<<grid, 128, 0, st>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
     else
-      k_sketch_fma<float, float><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
+      k_sketch_fma<float, float><<<grid, 128, 0, st>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<float*>(S));
     TSK_LAUNCH_CHECK(ctx, "k_sketch_fma<f32>");
   } else {
+    tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
     if (f64in)
-      k_sketch_fma<double, double><<<grid, 128, 0, ctx->stream>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<double*>(S));
+      k_sketch_fma<double, double><<<grid, 128, 0, st>>>(static_cast<const double*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<double*>(S));
     else
-      k_sketch_fma<float, double><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<double*>(S));
+      k_sketch_fma<float, double><<<grid, 128, 0, st>>>(static_cast<const float*>(T), d_cum, d_len, d_blk_prefix, n_series, d, R, k, stats, static_cast<double*>(S));
     TSK_LAUNCH_CHECK(ctx, "k_sketch_fma<f64>");
   }
   return TSK_OK;

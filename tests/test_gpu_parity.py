@@ -167,6 +167,22 @@ def test_sketch_build_matches_oracle(tsk, precision):
     assert np.all(np.abs(got - ref) <= tol * mag + 1e-30)
 
 
+@pytest.mark.parametrize("k", [65, 100, 130])
+def test_sketch_more_than_64_outputs(tsk, k):
+    """k beyond one group of 64 tensor-core outputs (the sketch-quality experiment uses k = ceil(sqrt(d)))."""
+    d, n = 300, 1500
+    rng = np.random.default_rng(110 + k)
+    T = np.cumsum(rng.normal(size=(d, n)), axis=1).astype(np.float32)
+    R = synth.count_sketch_R(d, k, 111) if k == 100 else synth.gaussian_R(d, k, 111)
+    S, _ = tsk.ts_sketch_build(_cuda(T.ravel()), _cuda(R), [n], d, precision="bf16")
+    tsk.sync()
+    Tbar, _, _ = o.global_znorm(T)
+    ref = o.sketch(Tbar, R, bf16=True)
+    got = S.cpu().numpy().astype(np.float64).reshape(k, n)
+    mag = np.abs(R.astype(np.float64)).T @ np.abs(Tbar)
+    assert np.all(np.abs(got - ref) <= 2e-6 * mag + 1e-30)
+
+
 def test_sketch_ragged_batch_and_count_sketch(tsk):
     d, k = 9, 3
     rng = np.random.default_rng(110)
