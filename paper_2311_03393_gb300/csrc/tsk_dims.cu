@@ -23,16 +23,19 @@
 //                   the loads are free of bank conflicts).  The largest key
 //                   rho - 1 and lowest window index merge per (series,
 //                   discord, stream) in a packed 64-bit word with atomicMax.
-//   3. k_dd_select  one warp per (series, discord): the chosen window of every
-//                   stream of the group is re-evaluated exactly (compensated
-//                   sums), then the strict running maximum over ascending j.
+//   3. k_dd_select  one CTA per (series, discord): warps take the streams of the
+//                   group in turn, a whole warp re-evaluates each chosen window
+//                   exactly (compensated sums), then the strict running maximum
+//                   over ascending j.
 //   4. k_dd_gather  (optional) copies stream j* of every discord into a
 //                   contiguous buffer for a self-join refinement profile.
 #include "tsk_internal.cuh"
+#include "tsk_ff.cuh"
 #include "tsk_rho.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 namespace {
 
@@ -56,35 +59,6 @@ struct DimArgs {
   int n_series, d, k, m, m4, excl, K;
 };
 
-// ---- float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi)/2) ----
-struct FF {
-  float h, l;
-};
-__device__ __forceinline__ FF ff_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ FF ff_fast(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const FF s = ff_two_sum(a.h, b.h);
-  return ff_fast(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ FF ff_sqr(FF a) {
-  const float p = __fmul_rn(a.h, a.h);
-  const float e = __fmaf_rn(a.h, a.h, -p);
-  return ff_fast(p, __fmaf_rn(__fmul_rn(2.0f, a.h), a.l, e));
-}
-__device__ __forceinline__ FF ff_mul(FF a, float b) {
-  const float p = __fmul_rn(a.h, b);
-  const float e = __fmaf_rn(a.h, b, -p);
-  return ff_fast(p, __fmaf_rn(a.l, b, e));
-}
 // x - x_ref as float-float: exact for float samples (two-sum), rounded to ~2^-48 for double samples
 __device__ __forceinline__ FF ff_shift(float x, float xr) { return ff_two_sum(x, -xr); }
 __device__ __forceinline__ FF ff_shift(double x, double xr) {
@@ -424,85 +398,128 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
   }
 }
 
-// float64 mean and the constant-window test of x[i .. i+m)
+// Exact re-evaluation of one chosen window by a whole warp: lanes take every
+// 32nd sample, float64 window means and the constant test, then the window
+// correlation with compensated float32 sums (products split exactly, running
+// sums as (hi, lo) pairs, the same arithmetic as the refinement kernel), the
+// lane partials added in float64.  Returns the distance; the whole warp calls it.
 template <typename TX>
-__device__ void window_mean_const(const TX* x, int i, int m, double* mean, bool* is_const) {
-  double s = 0.0;
-  for (int t = 0; t < m; ++t) s += static_cast<double>(x[i + t]);
-  const double mu = s / m;
-  double v = 0.0;
-  for (int t = 0; t < m; ++t) {
-    const double dv = static_cast<double>(x[i + t]) - mu;
-    v += dv * dv;
+__device__ double warp_window_dist(const TX* xq, int i, const TX* x, int t, int m) {
+  const int lane = threadIdx.x & 31;
+  double sq = 0.0, st = 0.0;
+  for (int u = lane; u < m; u += 32) {
+    sq += static_cast<double>(xq[i + u]);
+    st += static_cast<double>(x[t + u]);
   }
-  *mean = mu;
-  *is_const = (v / m) <= kConstRelVar * fmax(1.0, mu * mu);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_xor_sync(TSK_FULL_MASK, sq, o);
+    st += __shfl_xor_sync(TSK_FULL_MASK, st, o);
+  }
+  const double mq = sq / m, mt = st / m;
+  double vq = 0.0, vt = 0.0;
+  [[maybe_unused]] const float mqh = static_cast<float>(mq), mql = static_cast<float>(mq - static_cast<double>(mqh));
+  [[maybe_unused]] const float mth = static_cast<float>(mt), mtl = static_cast<float>(mt - static_cast<double>(mth));
+  double ab = 0.0, aa = 0.0, bb = 0.0;
+  if constexpr (std::is_same<TX, float>::value) {
+    tsk::DSum sab, saa, sbb;
+    for (int u = lane; u < m; u += 32) {
+      const double dq = static_cast<double>(xq[i + u]) - mq, dt = static_cast<double>(x[t + u]) - mt;
+      vq += dq * dq;
+      vt += dt * dt;
+      const float fa = __fsub_rn(__fsub_rn(xq[i + u], mqh), mql);
+      const float fb = __fsub_rn(__fsub_rn(x[t + u], mth), mtl);
+      sab.add_prod(fa, fb);
+      saa.add_prod(fa, fa);
+      sbb.add_prod(fb, fb);
+    }
+    ab = sab.value();
+    aa = saa.value();
+    bb = sbb.value();
+  } else {  // float64 series: float64 sums
+    for (int u = lane; u < m; u += 32) {
+      const double dq = static_cast<double>(xq[i + u]) - mq, dt = static_cast<double>(x[t + u]) - mt;
+      vq += dq * dq;
+      vt += dt * dt;
+      ab = fma(dq, dt, ab);
+      aa = fma(dq, dq, aa);
+      bb = fma(dt, dt, bb);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vq += __shfl_xor_sync(TSK_FULL_MASK, vq, o);
+    vt += __shfl_xor_sync(TSK_FULL_MASK, vt, o);
+    ab += __shfl_xor_sync(TSK_FULL_MASK, ab, o);
+    aa += __shfl_xor_sync(TSK_FULL_MASK, aa, o);
+    bb += __shfl_xor_sync(TSK_FULL_MASK, bb, o);
+  }
+  const bool cq = (vq / m) <= kConstRelVar * fmax(1.0, mq * mq);
+  const bool ct = (vt / m) <= kConstRelVar * fmax(1.0, mt * mt);
+  const double sqm = sqrt(static_cast<double>(m));
+  if (cq) return ct ? 0.0 : sqm;
+  if (ct) return sqm;
+  const double rho = ab / sqrt(aa * bb);
+  return sqrt(fmax(0.0, 2.0 * m * (1.0 - rho)));
 }
 
+// One CTA (8 warps) per (series, discord): warps take the streams j of the
+// group in turn and re-evaluate each chosen window exactly; then Alg. 3's
+// strict running maximum over ascending j (the larger score, then the lower j).
 template <typename TX>
 __global__ void __launch_bounds__(256) k_dd_select(const TX* __restrict__ Tq, const TX* __restrict__ T, DimArgs a,
-                                                   int32_t* __restrict__ dim,
-                                                   double* __restrict__ dim_score, int32_t* __restrict__ dim_nn,
-                                                   double* __restrict__ dim_scores) {
-  const int64_t wid = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= static_cast<int64_t>(a.n_series) * a.K) return;
-  const int s = static_cast<int>(wid / a.K);
+                                                   int32_t* __restrict__ dim, double* __restrict__ dim_score,
+                                                   int32_t* __restrict__ dim_nn, double* __restrict__ dim_scores) {
+  const int64_t sr = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kW = 8;
+  const int s = static_cast<int>(sr / a.K);
   const int n = a.len[s];
   const int l = n - a.m + 1;
-  const int i_star = a.idx[wid];
-  const int g_star = a.grp[wid];
+  const int i_star = a.idx[sr];
+  const int g_star = a.grp[sr];
   const bool valid = i_star >= 0 && i_star < l && g_star >= 0 && g_star < a.k;
-  double bs = 0.0;     // strict running maximum from 0 over this lane's j (ascending)
+  double bs = 0.0;  // strict running maximum from 0 over this warp's j (ascending)
   int bj = -1, bnn = -1;
-  int first = a.d;     // lowest j of the group
+  int first = a.d;  // lowest j of the group seen by this warp
   double first_s = 0.0;
   int first_nn = -1;
-  const double m2 = 2.0 * a.m;
-  const double sqm = sqrt(static_cast<double>(a.m));
-  for (int j = lane; j < a.d; j += 32) {
+  for (int j = warp; j < a.d; j += kW) {
     double sc = NAN;
     int nn = -1;
     if (valid && a.R[static_cast<int64_t>(j) * a.k + g_star] != 0.f) {
-      const TX* xq = Tq + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n;
-      const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * a.len_t[s];
-      const unsigned long long p = a.best[wid * a.d + j];
+      const unsigned long long p = a.best[sr * a.d + j];
       if (p == 0ull) {
         sc = INFINITY;  // no admissible neighbour
       } else {
         nn = tsk_unpack_idx(p);
-        double mq, mt;
-        bool cq, ct;
-        window_mean_const(xq, i_star, a.m, &mq, &cq);
-        window_mean_const(x, nn, a.m, &mt, &ct);
-        if (cq) sc = ct ? 0.0 : sqm;
-        else if (ct) sc = sqm;
-        else {
-          const double rho = tsk::window_rho(xq, i_star, x, nn, a.m, mq, mt);
-          sc = sqrt(fmax(0.0, m2 * (1.0 - rho)));
-        }
+        const TX* xq = Tq + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n;
+        const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * a.len_t[s];
+        sc = warp_window_dist(xq, i_star, x, nn, a.m);
       }
       if (j < first) { first = j; first_s = sc; first_nn = nn; }
       if (sc > bs) { bs = sc; bj = j; bnn = nn; }
     }
-    if (dim_scores) dim_scores[wid * a.d + j] = sc;
+    if (dim_scores && lane == 0) dim_scores[sr * a.d + j] = sc;
   }
-  // combine lanes: the larger score, then the lower j; and the lowest group member
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double os = __shfl_xor_sync(TSK_FULL_MASK, bs, o);
-    const int oj = __shfl_xor_sync(TSK_FULL_MASK, bj, o);
-    const int onn = __shfl_xor_sync(TSK_FULL_MASK, bnn, o);
-    if (oj >= 0 && (bj < 0 || os > bs || (os == bs && oj < bj))) { bs = os; bj = oj; bnn = onn; }
-    const int of = __shfl_xor_sync(TSK_FULL_MASK, first, o);
-    const double ofs = __shfl_xor_sync(TSK_FULL_MASK, first_s, o);
-    const int ofn = __shfl_xor_sync(TSK_FULL_MASK, first_nn, o);
-    if (of < first) { first = of; first_s = ofs; first_nn = ofn; }
-  }
+  __shared__ double sbs[kW], sfs[kW];
+  __shared__ int sbj[kW], sbn[kW], sfj[kW], sfn[kW];
   if (lane == 0) {
-    if (bj >= 0) { dim[wid] = bj; dim_score[wid] = bs; dim_nn[wid] = bnn; }
-    else if (first < a.d) { dim[wid] = first; dim_score[wid] = first_s; dim_nn[wid] = first_nn; }
-    else { dim[wid] = -1; dim_score[wid] = NAN; dim_nn[wid] = -1; }
+    sbs[warp] = bs; sbj[warp] = bj; sbn[warp] = bnn;
+    sfs[warp] = first_s; sfj[warp] = first; sfn[warp] = first_nn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    int j0 = -1, n0 = -1, f = a.d, fn = -1;
+    double fs = 0.0;
+    for (int w = 0; w < kW; ++w) {
+      if (sbj[w] >= 0 && (j0 < 0 || sbs[w] > b || (sbs[w] == b && sbj[w] < j0))) { b = sbs[w]; j0 = sbj[w]; n0 = sbn[w]; }
+      if (sfj[w] < f) { f = sfj[w]; fs = sfs[w]; fn = sfn[w]; }
+    }
+    if (j0 >= 0) { dim[sr] = j0; dim_score[sr] = b; dim_nn[sr] = n0; }
+    else if (f < a.d) { dim[sr] = f; dim_score[sr] = fs; dim_nn[sr] = fn; }
+    else { dim[sr] = -1; dim_score[sr] = NAN; dim_nn[sr] = -1; }
   }
 }
 
@@ -558,8 +575,7 @@ tsk_status run_dims(tsk_ctx* ctx, const TX* T, const TX* Tt, const DimArgs& a, i
     TSK_LAUNCH_CHECK(ctx, "k_dd_scan");
   }
   const int64_t warps = static_cast<int64_t>(a.n_series) * a.K;
-  k_dd_select<TX><<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(T, Tt, a, dim, dim_score, dim_nn,
-                                                                                     dim_scores);
+  k_dd_select<TX><<<static_cast<unsigned>(warps), 256, 0, st>>>(T, Tt, a, dim, dim_score, dim_nn, dim_scores);
   TSK_LAUNCH_CHECK(ctx, "k_dd_select");
   if (T_sel && total_samples > 0) {
     const int64_t total = total_samples * a.K;
