@@ -1,0 +1,145 @@
+"""The synthetic sketch-quality experiment (Sec. IV, "Synthetic Data").
+
+Random-walk series of d dimensions and n samples; the sketched method (Alg. 1
+count sketch with k = ceil(sqrt(d)), Alg. 2 on the k sketch streams, Alg. 3 for
+the dimension) returns one discord (i*, j*).  Its quality is the rank of the
+exact discord score of (i*, j*), the 1NN distance of window i* in dimension j*
+(Def. 6), among the scores of every (window, dimension) pair; a trial succeeds
+when that rank lies in the top 0.01 %.  The same is reported after the optional
+refinement (the top discord of dimension j*'s own profile).  The speedup
+compares the sketched path (sketch + k profiles + top-1 + Alg. 3, and with the
+refinement) with the exact d-dimensional path (d profiles + top-1), all timed
+with CUDA events.
+
+Every step runs through the library's entry points; the random walks are
+drawn on the device (cumulative sums of N(0, 1) steps from a seeded torch
+generator).
+
+  python -m paper_2311_03393_gb300.experiments --d 250 500 1000 --trials 20
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+import torch
+
+from . import api, synth
+
+
+def random_walks_device(d: int, n: int, seed: int, device) -> torch.Tensor:
+    """(d, n) float32 random walks, flattened stream-major, from a seeded device generator."""
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    steps = torch.randn((d, n), generator=g, device=device, dtype=torch.float32)
+    return torch.cumsum(steps, dim=1).reshape(-1).contiguous()
+
+
+def _timed(fn):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    out = fn()
+    b.record()
+    b.synchronize()
+    return out, a.elapsed_time(b)
+
+
+def trial(d: int, n: int, m: int, k: int, seed: int, device, top_frac: float = 1e-4,
+          sketch_precision: str = "bf16", R=None) -> dict:
+    """One trial: the sketched discord's rank among all exact (window, dimension) scores.
+
+    R: the (d, k) sketch matrix; default a seeded count sketch (Alg. 1).
+    """
+    excl = api.default_excl(m)
+    T = random_walks_device(d, n, seed, device)
+    if R is None:
+        R = synth.count_sketch_R(d, k, seed + 1)
+    R = torch.as_tensor(R, dtype=torch.float32).to(device)
+    l = n - m + 1
+
+    def sketched():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        S, _ = api.ts_sketch_build(T, R, [n], d, precision=sketch_precision)
+        ev[1].record()
+        P, I = api.mp_selfjoin(S, [n] * k, m, excl)
+        ev[2].record()
+        idx, grp, score, nn = api.discord_topk(P, I, [n], k, m, 1)
+        ev[3].record()
+        dims = api.dimension_detection(T, R, [n], d, m, idx, grp, excl, gather=True)
+        ev[4].record()
+        ev[4].synchronize()
+        parts = [ev[q].elapsed_time(ev[q + 1]) for q in range(4)]
+        return (idx, grp, dims), parts
+
+    def refine(dims):
+        return api.refine_dimensions(dims["T_sel"], [n], 1, m, excl)
+
+    def exact():
+        return api.exact_discords(T, [n], d, m, 1, excl)
+
+    torch.cuda.synchronize()
+    ((idx, grp, dims), parts), t_sk = _timed(sketched)
+    ref, t_ref = _timed(lambda: refine(dims))
+    ex, t_ex = _timed(exact)
+    i_star = int(idx[0, 0])
+    j_star = int(dims["dim"][0, 0])
+    i_ref = int(ref["idx"][0, 0])
+    P = ex["P"].view(d, n)[:, :l]
+    allowed = max(1, int(math.floor(top_frac * d * l)))
+
+    def rank_of(i, j):
+        return int((P > P[j, i]).sum().item()) + 1
+
+    rank, rank_ref = rank_of(i_star, j_star), rank_of(i_ref, j_star)
+    return {"i": i_star, "j": j_star, "score": float(P[j_star, i_star]), "rank": rank, "allowed": allowed,
+            "success": rank <= allowed, "i_refined": i_ref, "rank_refined": rank_ref,
+            "success_refined": rank_ref <= allowed, "exact_i": int(ex["idx"][0, 0]),
+            "exact_j": int(ex["grp"][0, 0]), "exact_score": float(ex["score"][0, 0]), "sketched_ms": t_sk,
+            "sketched_parts_ms": parts, "refine_ms": t_ref, "exact_ms": t_ex}
+
+
+def sketch_quality(d: int, n: int = 10000, m: int = 100, trials: int = 100, k: int | None = None,
+                   seed: int = synth.SEED_BASE, device=None, sketch_precision: str = "bf16") -> dict:
+    """Success rate and speedup over `trials` seeded random-walk trials (Sec. IV synthetic data)."""
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    k = int(math.ceil(math.sqrt(d))) if k is None else int(k)
+    # warm the layouts once (the first call builds and uploads them)
+    trial(d, n, m, k, seed + 999983, device, sketch_precision=sketch_precision)
+    rows = [trial(d, n, m, k, seed + 7919 * t, device, sketch_precision=sketch_precision) for t in range(trials)]
+    sk = float(np.median([r["sketched_ms"] for r in rows]))
+    ex = float(np.median([r["exact_ms"] for r in rows]))
+    rf = float(np.median([r["refine_ms"] for r in rows]))
+    parts = np.median(np.array([r["sketched_parts_ms"] for r in rows]), axis=0)
+    return {"d": d, "n": n, "m": m, "k": k, "trials": trials, "top_frac": 1e-4,
+            "success_rate": float(np.mean([r["success"] for r in rows])),
+            "success_rate_refined": float(np.mean([r["success_refined"] for r in rows])),
+            "median_rank": float(np.median([r["rank"] for r in rows])),
+            "median_rank_refined": float(np.median([r["rank_refined"] for r in rows])),
+            "exact_hit_rate": float(np.mean([r["i"] == r["exact_i"] and r["j"] == r["exact_j"] for r in rows])),
+            "sketched_ms": sk, "sketched_parts_ms": {"sketch": parts[0], "profiles": parts[1], "topk": parts[2],
+                                                     "dims": parts[3]},
+            "refine_ms": rf, "exact_ms": ex, "speedup": ex / sk if sk > 0 else None,
+            "speedup_with_refinement": ex / (sk + rf) if sk + rf > 0 else None,
+            "sketch_precision": sketch_precision}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--d", type=int, nargs="+", default=[250, 500, 1000, 2500, 5000, 7500, 10000])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--m", type=int, default=100)
+    ap.add_argument("--trials", type=int, default=100)
+    ap.add_argument("--seed", type=int, default=synth.SEED_BASE)
+    ap.add_argument("--sketch-precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    args = ap.parse_args(argv)
+    for d in args.d:
+        out = sketch_quality(d, args.n, args.m, args.trials, seed=args.seed, sketch_precision=args.sketch_precision)
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
