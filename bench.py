@@ -84,26 +84,33 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
-        self.rows = []
+        self.rows = []      # (monotonic time, fields)
         self.proc = None
         self.thread = None
+        self.window = None  # (start, end) of the timed region
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            deadline = time.monotonic() + 5.0  # the first sample arrives before the timed region starts
+            while not self.rows and time.monotonic() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
+
+    def mark(self, start: float, end: float):
+        self.window = (start, end)
 
     def _read(self):
         for line in self.proc.stdout:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((time.monotonic(), parts))
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -115,14 +122,24 @@ class ClockSampler:
             self.thread.join(timeout=5)
 
     def summary(self):
-        if not self.rows:
+        rows = self.rows
+        if self.window is not None:
+            a, b = self.window
+            inside = [r for t, r in rows if a <= t <= b + 0.06]  # a sample just after the end covers the tail
+            if not inside:  # a region shorter than the sampling interval: the samples around it
+                near = sorted(rows, key=lambda tr: min(abs(tr[0] - a), abs(tr[0] - b)))[:2]
+                inside = [r for _, r in near]
+            rows = inside
+        else:
+            rows = [r for _, r in rows]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[q] for r in self.rows for q in range(4) if r[5 + q].lower() == "active"})
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 # ---------------------------------------------------------------------------
@@ -312,6 +329,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     launches0 = tsk.launch_count()
     with ClockSampler(torch.cuda.current_device()) as clk:
+        t_region = time.monotonic()
         for s in range(args.steps):
             flush.fill_(float(s))
             if graph is None:
@@ -323,6 +341,8 @@ def run_gpu(args):
                 for i in range(1, 5):
                     ev[s][i].record(stream)
         torch.cuda.synchronize()
+        clk.mark(t_region, time.monotonic())
+        time.sleep(0.08)  # let the sample after the region arrive
     launches = tsk.launch_count() - launches0
     if graph is not None:
         launches = launches_per_step * args.steps  # the replayed graph holds one step's launches
@@ -399,7 +419,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "series": ns, "parallelism": f"replicas{ws}",
                    "sketch": "bf16 tensor cores, f32 accumulate",
-                   "mp": "f32 diagonal recurrence, f64 anchors, exact refinement", "l2": "flushed before each step",
+                   "mp": "f32 diagonal recurrence, periodic anchors from centred values, exact refinement", "l2": "flushed before each step",
                    "cells_per_step": cells_step, "top_k": K, "cuda_graph": graph is not None,
                    "tile_rows": {"sketch": autotune.rows_for(slen_k, m, excl),
                                  "exact": autotune.rows_for(slen_d, m, excl)}},

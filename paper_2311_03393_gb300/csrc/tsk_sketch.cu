@@ -152,8 +152,8 @@ __global__ void k_sketch_prep(const float* __restrict__ R, int32_t d, int32_t k,
   }
 }
 
-template <typename TIn>
-__global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restrict__ T, const int64_t* __restrict__ cum,
+template <typename TIn, int NTM>
+__global__ void __launch_bounds__(kSkThreads, (NTM <= 4 ? 6 : 4)) k_sketch_bf16(const TIn* __restrict__ T, const int64_t* __restrict__ cum,
                                                            const int32_t* __restrict__ len,
                                                            const int64_t* __restrict__ blk_prefix, int32_t n_series,
                                                            int32_t d, int32_t dchunk, const uint16_t* __restrict__ Rt,
@@ -171,13 +171,13 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restric
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gid = lane >> 2, tig = lane & 3;
   const int gbase = static_cast<int>(blockIdx.y) * 64;
-  const int NT = min(8, (k - gbase + 7) >> 3);
+  const int NT = min(NTM, (k - gbase + 7) >> 3);  // n8 tiles of this output group (NTM: at most)
   const int jb = static_cast<int>(blockIdx.z) * dchunk;
   const int je = min(d, jb + dchunk);
 
-  float acc[8][4];
+  float acc[NTM][4];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+  for (int q = 0; q < NTM; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
 
   // this thread's share of a stage: 16 samples (dimension e >> 6, time e & 63 for
   // e = tid + 128 u) and two 8-wide rows of R (output e2 >> 2, dimensions 8 (e2 & 3)..)
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restric
       const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * tig + 8]);
       const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * tig + 8]);
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
+      for (int nt = 0; nt < NTM; ++nt) {
         if (nt < NT) {
           const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][ks + 2 * tig]);
           const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][ks + 2 * tig + 8]);
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_bf16(const TIn* __restric
     }
   }
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
+  for (int nt = 0; nt < NTM; ++nt) {
     if (nt < NT) {
       const int g = gbase + nt * 8 + 2 * tig;
       const int t = t0 + warp * 16 + gid;
@@ -460,15 +460,27 @@ tsk_status tsk_launch_sketch(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n
     float* out = parts > 1 ? part : static_cast<float*>(S);
     const int64_t pstride = static_cast<int64_t>(k) * total_samples;
     {
+      // accumulator tiles per thread: as many n8 tiles as the widest output group needs
+      const int nt = std::min(8, (k + 7) / 8);
+      const int ntm = nt <= 1 ? 1 : nt <= 2 ? 2 : nt <= 4 ? 4 : 8;
       tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
-      if (f64in)
-        k_sketch_bf16<double><<<grid_bf16, kSkThreads, 0, st>>>(static_cast<const double*>(T), d_cum, d_len,
-                                                                  d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc,
-                                                                  out, pstride);
-      else
-        k_sketch_bf16<float><<<grid_bf16, kSkThreads, 0, st>>>(static_cast<const float*>(T), d_cum, d_len,
-                                                                 d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc,
-                                                                 out, pstride);
+      if (f64in) {
+        const double* Td = static_cast<const double*>(T);
+        switch (ntm) {
+          case 1: k_sketch_bf16<double, 1><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          case 2: k_sketch_bf16<double, 2><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          case 4: k_sketch_bf16<double, 4><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          default: k_sketch_bf16<double, 8><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+        }
+      } else {
+        const float* Tf = static_cast<const float*>(T);
+        switch (ntm) {
+          case 1: k_sketch_bf16<float, 1><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          case 2: k_sketch_bf16<float, 2><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          case 4: k_sketch_bf16<float, 4><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          default: k_sketch_bf16<float, 8><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+        }
+      }
     }
     TSK_LAUNCH_CHECK(ctx, "k_sketch_bf16");
     if (parts > 1) {
