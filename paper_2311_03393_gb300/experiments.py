@@ -18,6 +18,7 @@ drawn on the device (cumulative sums of N(0, 1) steps from a seeded torch
 generator).
 
   python -m paper_2311_03393_gb300.experiments --d 250 500 1000 --trials 20
+  python -m paper_2311_03393_gb300.experiments sketch --d 1024 --n 100000 --k 16
 """
 from __future__ import annotations
 
@@ -135,15 +136,56 @@ def sketch_quality(d: int, n: int = 10000, m: int = 100, trials: int = 100, k: i
             "sketch_precision": sketch_precision}
 
 
+def sketch_throughput(d: int, n: int, k: int, reps: int = 5, seed: int = synth.SEED_BASE, precision: str = "bf16",
+                      device=None) -> dict:
+    """Time ts_sketch_build's sketch kernel on one (d, n) random-walk series with a Gaussian R (d x k).
+
+    Reports the kernel's device time per launch (library events) and its
+    algorithmic bytes per second, 4 d n (T) + 4 k n (S).
+    """
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    T = random_walks_device(d, n, seed, device)
+    R = torch.from_numpy(synth.gaussian_R(d, k, seed + 1)).to(device)
+    for _ in range(3):
+        api.ts_sketch_build(T, R, [n], d, precision=precision)
+    api.sync()
+    api.profile_enable(True)
+    api.profile_read("sketch")
+    for _ in range(reps):
+        api.ts_sketch_build(T, R, [n], d, precision=precision)
+    api.sync()
+    ms, launches = api.profile_read("sketch")
+    api.profile_enable(False)
+    per = ms / max(launches, 1)
+    return {"d": d, "n": n, "k": k, "precision": precision, "ms_per_launch": per,
+            "gb_per_s": (4.0 * d * n + 4.0 * k * n) / (per / 1e3) / 1e9}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--d", type=int, nargs="+", default=[250, 500, 1000, 2500, 5000, 7500, 10000])
-    ap.add_argument("--n", type=int, default=10000)
-    ap.add_argument("--m", type=int, default=100)
-    ap.add_argument("--trials", type=int, default=100)
-    ap.add_argument("--seed", type=int, default=synth.SEED_BASE)
-    ap.add_argument("--sketch-precision", default="bf16", choices=["bf16", "fp32", "fp64"])
-    args = ap.parse_args(argv)
+    sub = ap.add_subparsers(dest="cmd")
+    q = sub.add_parser("quality", help="success rate and speedup over d (the default)")
+    q.add_argument("--d", type=int, nargs="+", default=[250, 500, 1000, 2500, 5000, 7500, 10000])
+    q.add_argument("--n", type=int, default=10000)
+    q.add_argument("--m", type=int, default=100)
+    q.add_argument("--trials", type=int, default=100)
+    q.add_argument("--seed", type=int, default=synth.SEED_BASE)
+    q.add_argument("--sketch-precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    t = sub.add_parser("sketch", help="throughput of the sketch kernel on one series")
+    t.add_argument("--d", type=int, default=1024)
+    t.add_argument("--n", type=int, default=100000)
+    t.add_argument("--k", type=int, default=16)
+    t.add_argument("--reps", type=int, default=5)
+    t.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    argv = list(argv) if argv is not None else None
+    import sys
+    raw = sys.argv[1:] if argv is None else argv
+    if not raw or raw[0].startswith("-"):
+        raw = ["quality"] + raw
+    args = ap.parse_args(raw)
+    if args.cmd == "sketch":
+        print(json.dumps(sketch_throughput(args.d, args.n, args.k, args.reps, precision=args.precision)), flush=True)
+        return
     for d in args.d:
         out = sketch_quality(d, args.n, args.m, args.trials, seed=args.seed, sketch_precision=args.sketch_precision)
         print(json.dumps(out), flush=True)
