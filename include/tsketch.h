@@ -216,14 +216,14 @@ TSK_API tsk_status mp_selfjoin(tsk_ctx* ctx, const void* X, int32_t x_dtype, int
  *   A, B        : device streams, packed like mp_selfjoin's X (A: n_pairs
  *                 streams of len_a_host[q] samples; B: n_pairs streams of
  *                 len_b_host[q]); both float32 or both float64 (x_dtype).
- *   P_a, I_a    : device float32 / int32, packed like A (entries past the
- *                 last window are NaN / -1).
- *   P_b, I_b    : optional (both NULL to skip), packed like B.
- *   precision   : TSK_MP_FP32 (the float32 recurrence with float64 anchors and
- *                 an exact re-evaluation of each chosen neighbour);
- *                 TSK_MP_FP64 returns TSK_ERR_UNSUPPORTED.
+ *   P_a, I_a    : device float32 (float64 for TSK_MP_FP64) / int32, packed like
+ *                 A (entries past the last window are NaN / -1).
+ *   P_b, I_b    : optional (both NULL to skip), packed like B, same types.
+ *   precision   : TSK_MP_FP32 (the float32 recurrence with periodic anchors and
+ *                 an exact re-evaluation of each chosen neighbour) or
+ *                 TSK_MP_FP64 (float64 throughout, lowest index on ties).
  * Errors: TSK_ERR_INVALID_ARG for NULL required arrays, only one of P_b / I_b,
- * a bad dtype, m outside [2, 4096] or a stream shorter than m.
+ * a bad dtype or precision, m outside [2, 4096] or a stream shorter than m.
  */
 TSK_API tsk_status mp_abjoin(tsk_ctx* ctx, const void* A, const void* B, int32_t x_dtype, int32_t n_pairs,
                              const int32_t* len_a_host, const int32_t* len_b_host, int32_t m, int32_t precision,

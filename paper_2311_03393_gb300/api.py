@@ -176,11 +176,12 @@ def mp_selfjoin(X: torch.Tensor, stream_len: Sequence[int], m: int, excl: int | 
 
 
 def mp_abjoin(A: torch.Tensor, B: torch.Tensor, len_a: Sequence[int], len_b: Sequence[int], m: int,
-              train_profile: bool = False):
+              train_profile: bool = False, precision: str = "fp32"):
     """AB-join profiles (Def. 6): each test window of A_q against every window of B_q.
 
     Returns (P_a, I_a) packed like A, plus (P_b, I_b) packed like B when
-    train_profile (each training window's nearest test window).
+    train_profile (each training window's nearest test window).  precision
+    'fp64' is the exact float64 mode (P float64).
     """
     _need_cuda(A, B)
     if A.dtype != B.dtype:
@@ -189,14 +190,15 @@ def mp_abjoin(A: torch.Tensor, B: torch.Tensor, len_a: Sequence[int], len_b: Seq
     if len(len_b) != n:
         raise ValueError("len_a and len_b must have one entry per stream pair")
     dev = A.device
-    P_a = torch.empty(A.numel(), dtype=torch.float32, device=dev)
+    pdt = torch.float64 if precision == "fp64" else torch.float32
+    P_a = torch.empty(A.numel(), dtype=pdt, device=dev)
     I_a = torch.empty(A.numel(), dtype=torch.int32, device=dev)
-    P_b = torch.empty(B.numel(), dtype=torch.float32, device=dev) if train_profile else None
+    P_b = torch.empty(B.numel(), dtype=pdt, device=dev) if train_profile else None
     I_b = torch.empty(B.numel(), dtype=torch.int32, device=dev) if train_profile else None
     la, lap = _i32_array(len_a)
     lb, lbp = _i32_array(len_b)
     h = _ctx(dev)
-    N.check(N.lib().mp_abjoin(h, _ptr(A), _ptr(B), _dtype_code(A), n, lap, lbp, int(m), MP_PRECISION["fp32"],
+    N.check(N.lib().mp_abjoin(h, _ptr(A), _ptr(B), _dtype_code(A), n, lap, lbp, int(m), MP_PRECISION[precision],
                               _ptr(P_a), _ptr(I_a), _ptr(P_b) if train_profile else None,
                               _ptr(I_b) if train_profile else None), h, "mp_abjoin")
     return (P_a, I_a, P_b, I_b) if train_profile else (P_a, I_a)

@@ -278,7 +278,7 @@ tsk_status mp_plan(tsk_ctx* ctx, int32_t n, const int32_t* lens, const uint8_t* 
 // AB join: streams 0..n-1 are the test streams, n..2n-1 their training
 // partners.  Test rows against training columns on diagonals >= 0, then
 // training rows against test columns on diagonals >= 1.
-tsk_status mp_plan_ab(tsk_ctx* ctx, int32_t n, const int32_t* len_a, const int32_t* len_b, int32_t m,
+tsk_status mp_plan_ab(tsk_ctx* ctx, int32_t n, const int32_t* len_a, const int32_t* len_b, int32_t m, int32_t prec,
                       tsk_mp_plan* plan) {
   const int32_t D = tsk_mp_band_width();
   int32_t H = ctx->mp_H;
@@ -288,8 +288,8 @@ tsk_status mp_plan_ab(tsk_ctx* ctx, int32_t n, const int32_t* len_a, const int32
     H = auto_rows(ctx, cells);
   }
   std::string key = "mpab";
-  const int32_t hdr[4] = {n, m, H, D};
-  append(key, hdr, 4);
+  const int32_t hdr[5] = {n, m, H, D, prec};
+  append(key, hdr, 5);
   append(key, len_a, n);
   append(key, len_b, n);
   tsk_status st = TSK_OK;
@@ -308,20 +308,25 @@ tsk_status mp_plan_ab(tsk_ctx* ctx, int32_t n, const int32_t* len_a, const int32
     const int32_t chunk_rows = tsk_mp_chunk_rows();
     for (int q = 0; q < N; ++q) {
       const int64_t l = static_cast<int64_t>(len[q]) - m + 1;
+      const int p = q < n ? q + n : q - n;
+      const int64_t lp = static_cast<int64_t>(len[p]) - m + 1;
       xoff[q + 1] = xoff[q] + len[q];
       woff[q + 1] = woff[q] + ((l + pad + 3) & ~int64_t(3));
       chp[q + 1] = chp[q] + (l + chunk - 1) / chunk;
+      // float64 path: one thread per diagonal, diagonals 0.. (test rows) or 1.. (training rows)
+      tp[q + 1] = tp[q] + (prec == TSK_MP_FP64 ? std::max<int64_t>(0, q < n ? lp : lp - 1) : 0);
     }
-    for (int q = 0; q < N; ++q) {
-      const int p = q < n ? q + n : q - n;
-      add_units(q, static_cast<int64_t>(len[q]) - m + 1, static_cast<int64_t>(len[p]) - m + 1, q < n ? 0 : 1, H, D,
-                chunk_rows, tiles_int, tiles_tri);
-    }
+    if (prec != TSK_MP_FP64)
+      for (int q = 0; q < N; ++q) {
+        const int p = q < n ? q + n : q - n;
+        add_units(q, static_cast<int64_t>(len[q]) - m + 1, static_cast<int64_t>(len[p]) - m + 1, q < n ? 0 : 1, H,
+                  D, chunk_rows, tiles_int, tiles_tri);
+      }
     tiles_int.insert(tiles_int.end(), tiles_tri.begin(), tiles_tri.end());
     meta.assign(11, 0);
     meta[0] = woff[N];
     meta[1] = chp[N];
-    meta[2] = static_cast<int64_t>(tiles_int.size() / 4);
+    meta[2] = prec == TSK_MP_FP64 ? tp[N] : static_cast<int64_t>(tiles_int.size() / 4);
     meta[3] = xoff[N];
     meta[4] = static_cast<int64_t>(put(buf, xoff));
     meta[5] = static_cast<int64_t>(put(buf, len));
@@ -339,7 +344,7 @@ tsk_status mp_plan_ab(tsk_ctx* ctx, int32_t n, const int32_t* len_a, const int32
   plan->excl = 0;
   plan->H = H;
   plan->D = D;
-  plan->prec = TSK_MP_FP32;
+  plan->prec = prec;
   plan->total_windows = b->meta[0];
   plan->total_chunks = b->meta[1];
   plan->total_tiles = b->meta[2];
@@ -734,16 +739,17 @@ extern "C" TSK_API tsk_status mp_abjoin(tsk_ctx* ctx, const void* A, const void*
   if ((P_b == nullptr) != (I_b == nullptr))
     return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: P_b and I_b must be both NULL or both non-NULL");
   if (x_dtype != TSK_F32 && x_dtype != TSK_F64) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: bad x_dtype");
-  if (precision != TSK_MP_FP32)
-    return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "mp_abjoin: only TSK_MP_FP32 is implemented for the AB join");
+  if (precision != TSK_MP_FP32 && precision != TSK_MP_FP64)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: bad precision");
   if (n_pairs < 1) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: n_pairs must be >= 1");
   if (m < 2 || m > 4096) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_abjoin: need 2 <= m <= 4096 (got %d)", m);
   if ((st = check_lens(ctx, n_pairs, len_a_host, m, "mp_abjoin (test)"))) return st;
   if ((st = check_lens(ctx, n_pairs, len_b_host, m, "mp_abjoin (train)"))) return st;
   tsk_mp_plan plan;
-  if ((st = mp_plan_ab(ctx, n_pairs, len_a_host, len_b_host, m, &plan))) return st;
+  if ((st = mp_plan_ab(ctx, n_pairs, len_a_host, len_b_host, m, precision, &plan))) return st;
   if ((st = tsk_ws_require(ctx, tsk_mp_ws_bytes(plan, 2 * n_pairs)))) return st;
-  return tsk_run_mp_ab(ctx, A, B, x_dtype, n_pairs, plan, m, P_a, I_a, P_b, I_b, static_cast<char*>(ctx->ws));
+  return tsk_run_mp_ab(ctx, A, B, x_dtype, n_pairs, plan, m, precision, P_a, I_a, P_b, I_b,
+                       static_cast<char*>(ctx->ws));
 }
 
 extern "C" TSK_API tsk_status discord_topk(tsk_ctx* ctx, const void* P, int32_t p_dtype, const int32_t* I,

@@ -199,8 +199,8 @@ tsk_status tsk_run_mp(tsk_ctx* ctx, const void* X, int x_dtype, int32_t n_stream
 // AB join: n_pairs test streams (A) against their training partners (B); the
 // plan covers the 2 n_pairs streams, test streams first.
 tsk_status tsk_run_mp_ab(tsk_ctx* ctx, const void* A, const void* B, int x_dtype, int32_t n_pairs,
-                         const tsk_mp_plan& plan, int32_t m, void* P_a, int32_t* I_a, void* P_b, int32_t* I_b,
-                         char* ws);
+                         const tsk_mp_plan& plan, int32_t m, int32_t precision, void* P_a, int32_t* I_a, void* P_b,
+                         int32_t* I_b, char* ws);
 size_t tsk_mp_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams);
 int tsk_mp_band_width();
 // Aggregation and ranked discords.

@@ -669,41 +669,48 @@ __device__ __forceinline__ double f64_cell_rho(double cov, const double* inv64, 
   return cov * inv64[i] * inv64[j];
 }
 
-template <typename TX>
+template <typename TX, bool AB>
 __global__ void __launch_bounds__(128) k_mp_diag_f64(MpArgs a, int pass) {
   const int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= a.total_tiles) return;
   const int q = tsk_find_segment<int64_t>(a.tile_prefix, a.n_streams, w);
-  const int n = a.len[q];
+  const int p = AB ? (q < a.split ? q + a.split : q - a.split) : q;  // the column side
   const int m = a.m;
-  const int l = n - m + 1;
-  const int delta = a.excl + static_cast<int>(w - a.tile_prefix[q]);
-  const TX* x = static_cast<const TX*>(a.X) + a.xoff[q];
-  const int64_t wb = a.woff[q];
+  const int l = a.len[q] - m + 1, lp = a.len[p] - m + 1;
+  const int dmin = AB ? (q < a.split ? 0 : 1) : a.excl;
+  const int delta = dmin + static_cast<int>(w - a.tile_prefix[q]);
+  const TX* X = static_cast<const TX*>(a.X);
+  const TX* x = AB ? stream_base(X, static_cast<const TX*>(a.X2), a.xoff, a.split, q) : X + a.xoff[q];
+  const TX* xp = AB ? stream_base(X, static_cast<const TX*>(a.X2), a.xoff, a.split, p) : x;
+  const int64_t wb = a.woff[q], wbp = a.woff[p];
   const double* mu = a.wa.mu + wb;
+  const double* mup = a.wa.mu + wbp;
   const double* inv64 = a.wa.inv64 + wb;
+  const double* inv64p = a.wa.inv64 + wbp;
   unsigned long long* best = a.wa.best + wb;
+  unsigned long long* bestp = a.wa.best + wbp;
   int32_t* bidx = a.wa.bidx + wb;
+  int32_t* bidxp = a.wa.bidx + wbp;
   double cov = 0.0;
   const double m0 = mu[0];
-  for (int t = 0; t < m; ++t) cov = fma(static_cast<double>(x[t]) - m0, static_cast<double>(x[delta + t]), cov);
-  for (int i = 0; i + delta < l; ++i) {
+  for (int t = 0; t < m; ++t) cov = fma(static_cast<double>(x[t]) - m0, static_cast<double>(xp[delta + t]), cov);
+  for (int i = 0; i < l && i + delta < lp; ++i) {
     const int j = i + delta;
-    const double rho = cov * inv64[i] * inv64[j];
+    const double rho = cov * inv64[i] * inv64p[j];
     const unsigned long long key = tsk_ordered_u64(rho);
     if (pass == 0) {
       atomicMax(&best[i], key);
-      atomicMax(&best[j], key);
+      atomicMax(&bestp[j], key);
     } else {
       if (key == best[i]) atomicMin(&bidx[i], j);
-      if (key == best[j]) atomicMin(&bidx[j], i);
+      if (key == bestp[j]) atomicMin(&bidxp[j], i);
     }
-    if (j + 1 < l) {
+    if (i + 1 < l && j + 1 < lp) {
       const double xa = static_cast<double>(x[i]), xb = static_cast<double>(x[i + m]);
-      const double ya = static_cast<double>(x[j]), yb = static_cast<double>(x[j + m]);
+      const double ya = static_cast<double>(xp[j]), yb = static_cast<double>(xp[j + m]);
       const double dfi = (xb - xa) * 0.5, dfj = (yb - ya) * 0.5;
       const double dgi = (xb - mu[i + 1]) + (xa - mu[i]);
-      const double dgj = (yb - mu[j + 1]) + (ya - mu[j]);
+      const double dgj = (yb - mup[j + 1]) + (ya - mup[j]);
       cov = fma(dfi, dgj, cov);
       cov = fma(dfj, dgi, cov);
     }
@@ -872,7 +879,10 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
     if (f64) {
       const int64_t blocks = (plan.total_tiles + 127) / 128;
       for (int pass = 0; pass < 2; ++pass) {
-        k_mp_diag_f64<TX><<<static_cast<unsigned>(blocks), 128, 0, st>>>(a, pass);
+        if (ab)
+          k_mp_diag_f64<TX, true><<<static_cast<unsigned>(blocks), 128, 0, st>>>(a, pass);
+        else
+          k_mp_diag_f64<TX, false><<<static_cast<unsigned>(blocks), 128, 0, st>>>(a, pass);
         TSK_LAUNCH_CHECK(ctx, "k_mp_diag_f64");
       }
     } else {
@@ -896,7 +906,11 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
   if (total > 0) {
     const int64_t blocks = (total + 255) / 256;
     const unsigned g = static_cast<unsigned>(blocks);
-    if (f64)
+    if (f64 && ab)
+      k_mp_refine<TX, double, true><<<g, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.smask, plan.woff,
+                                                       n_streams, total, m, 0, 1, wa, static_cast<double*>(P), I,
+                                                       static_cast<double*>(P2), I2);
+    else if (f64)
       k_mp_refine<TX, double, false><<<g, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.smask, plan.woff,
                                                         n_streams, total, m, excl, 1, wa, static_cast<double*>(P), I,
                                                         nullptr, nullptr);
@@ -939,13 +953,13 @@ tsk_status tsk_run_mp(tsk_ctx* ctx, const void* X, int x_dtype, int32_t n_stream
 }
 
 tsk_status tsk_run_mp_ab(tsk_ctx* ctx, const void* A, const void* B, int x_dtype, int32_t n_pairs,
-                         const tsk_mp_plan& plan, int32_t m, void* P_a, int32_t* I_a, void* P_b, int32_t* I_b,
-                         char* ws) {
+                         const tsk_mp_plan& plan, int32_t m, int32_t precision, void* P_a, int32_t* I_a, void* P_b,
+                         int32_t* I_b, char* ws) {
   if (x_dtype == TSK_F64)
     return run_typed<double>(ctx, static_cast<const double*>(A), static_cast<const double*>(B), n_pairs, true,
-                             2 * n_pairs, plan, m, 0, TSK_MP_FP32, P_a, I_a, P_b, I_b, ws);
+                             2 * n_pairs, plan, m, 0, precision, P_a, I_a, P_b, I_b, ws);
   return run_typed<float>(ctx, static_cast<const float*>(A), static_cast<const float*>(B), n_pairs, true, 2 * n_pairs,
-                          plan, m, 0, TSK_MP_FP32, P_a, I_a, P_b, I_b, ws);
+                          plan, m, 0, precision, P_a, I_a, P_b, I_b, ws);
 }
 
 // ---------------------------------------------------------------------------

@@ -125,3 +125,32 @@ def test_sketched_and_exact_ab_discords_match_the_oracle(tsk):
     got_e = list(zip(*(ex[key].cpu().numpy()[0] for key in ("idx", "grp", "score", "nn"))))
     check_discords(got_e, ref_e, A_e, tie_rel=1e-3)
     assert got_e[0][1] == 2
+
+
+def test_float64_ab_join_is_exact(tsk):
+    """TSK_MP_FP64: every test and training window's profile value to 1e-9, neighbours exactly."""
+    rng = np.random.default_rng(54)
+    m = 30
+    la, lb = [900, 400], [500, 1300]
+    A = [np.cumsum(rng.normal(size=n)) for n in la]
+    B = [np.cumsum(rng.normal(size=n)) for n in lb]
+    A[1][100:160] = 3.0                                     # constant test windows
+    P_a, I_a, P_b, I_b = tsk.mp_abjoin(_pack(A, torch.float64), _pack(B, torch.float64), la, lb, m,
+                                       train_profile=True, precision="fp64")
+    tsk.sync()
+    assert P_a.dtype == torch.float64
+    P_a, I_a, P_b, I_b = (t.cpu().numpy() for t in (P_a, I_a, P_b, I_b))
+    oa = np.concatenate([[0], np.cumsum(la)])
+    ob = np.concatenate([[0], np.cumsum(lb)])
+    for q in range(2):
+        for (x, y, P, I, off) in ((A[q], B[q], P_a, I_a, oa[q]), (B[q], A[q], P_b, I_b, ob[q])):
+            l = len(x) - m + 1
+            P_ref, I_ref = o.mp_abjoin(x, y, m)
+            np.testing.assert_allclose(P[off:off + l], P_ref, rtol=1e-9, atol=1e-9)
+            diff = np.flatnonzero(I[off:off + l] != I_ref)
+            if diff.size:  # equal distances (e.g. a constant window against non-constant ones: sqrt(m) each)
+                Zx, _, _, _ = o.znorm_windows(x, m)
+                Zy, _, _, _ = o.znorm_windows(y, m)
+                for i in diff:
+                    dij = float(np.linalg.norm(Zx[i] - Zy[I[off + i]]))
+                    assert abs(dij - P_ref[i]) <= 1e-9 * max(1.0, P_ref[i]), (i, I[off + i], I_ref[i])
