@@ -73,9 +73,11 @@ enum {
 
 /* arithmetic of the matrix profile */
 enum {
-  TSK_MP_FP32 = 0, /* float32 diagonal recurrence with float64 anchors, then an exact
-                      re-evaluation of every row's chosen neighbour (compensated
-                      float32 sums for float32 input); P is float32             */
+  TSK_MP_FP32 = 0, /* float32 diagonal recurrence from periodic anchors (float32
+                      from centred values for float32 input, float64 for float64
+                      input, at most 8192 rows apart), then an exact re-evaluation
+                      of every row's chosen neighbour (compensated float32 sums
+                      for float32 input); P is float32                          */
   TSK_MP_FP64 = 1  /* float64 throughout; P is float64                            */
 };
 
@@ -102,7 +104,7 @@ TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s);
 /* Rows per matrix-profile work unit (a band of 512 diagonals x `rows` rows):
  * 0 = automatic (about 64 units per resident warp, 2048..8192), else a
  * multiple of 32 in [32, 1 << 20].  Smaller units balance short streams,
- * larger ones amortise the float64 anchors. */
+ * larger ones amortise the anchors. */
 TSK_API tsk_status tsk_set_tile_rows(tsk_ctx* ctx, int32_t rows);
 /* Number of kernels this context has launched since creation. */
 TSK_API int64_t tsk_launch_count(const tsk_ctx* ctx);

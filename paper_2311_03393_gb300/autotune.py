@@ -1,7 +1,7 @@
 """Work-unit autotuner for the matrix-profile kernel.
 
 The diagonal kernel splits each band of 512 diagonals into work units of a
-given number of rows.  Larger units start fewer exact float64 anchors, smaller
+given number of rows.  Larger units start fewer anchors, smaller
 units balance the last wave better; the best height depends on the GPU, the
 subsequence length and the size and shape of the stream layout.  `tune` times
 mp_selfjoin at a few candidate heights with the library's own CUDA-event

@@ -14,7 +14,8 @@
 //                       of 512 diagonals (two half bands of 256 walked in
 //                       lockstep as float2 pairs) and a run of rows; lane t walks
 //                       8 diagonals of each half down the rows with the float32
-//                       recurrence, anchored exactly in float64 at the first row.
+//                       recurrence from an anchor at the first row (float32 from
+//                       centred values for float32 series, float64 otherwise).
 //                       Each cell's key rho - 1 (rho = c * inv_i * inv_j) updates
 //                       the row maximum (reduced over lanes through shared memory)
 //                       and the column maximum (carried from lane to lane as the
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_mp_diag(MpArgs a) {
   MpWarpSmem& w = reinterpret_cast<MpWarpSmem*>(mp_smem)[wid];
   for (;;) {
     // guided claim: a run of consecutive work units, long while much work
-    // remains (contiguous units of a band then share one float64 anchor),
+    // remains (contiguous units of a band then share one anchor),
     // single units at the end (balance)
     int w0 = 0, wend = 0;
     if (lane == 0) {
