@@ -42,6 +42,15 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kWinPerThread = 8;                      // consecutive windows per thread
 constexpr int kTW = kScanThreads * kWinPerThread;     // 2048 windows per scan item
+constexpr int kQB = 16;                               // discords staged per batch (at most; even)
+constexpr int kQBudget = 8192;                        // floats of staged queries (32 KB)
+
+// discords staged per batch for subsequence length m (even, 2..kQB)
+__host__ __device__ inline int query_batch(int m) {
+  const int m4 = (m + 3) & ~3;
+  const int q = kQBudget / m4;
+  return q >= kQB ? kQB : (q < 2 ? 2 : (q & ~1));
+}
 constexpr double kConstRelVar = 1e-12;
 
 struct DimArgs {
@@ -195,15 +204,16 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
   const int ns_max = kTW + m4 + 8;                             // staged samples (zero padded)
   float* xs = reinterpret_cast<float*>(smem_raw);              // [xs_phys(ns_max)]
   const int xs_words = ns_max + 8;
-  float* qs = xs + xs_words;                                   // [2 * m4] one query, or two interleaved
-  float* w_inv = qs + 2 * m4;                                  // [kTW] 1/||window - mean|| (0: constant)
+  const int qb = query_batch(m);
+  float* qbuf = xs + xs_words;                                 // [qb * m4] staged queries (pairs interleaved)
+  float* w_inv = qbuf + qb * m4;                               // [kTW] 1/||window - mean|| (0: constant)
   float* w_mean = w_inv + kTW;                                 // [kTW] window mean of the shifted samples
   float* p1h = w_mean + kTW;                                   // [kTW + m] prefix of shifted samples (float-float)
   float* p1l = p1h + (kTW + m);
   float* p2h = p1l + (kTW + m);                                // [kTW + m] prefix of their squares
   float* p2l = p2h + (kTW + m);
   __shared__ float segs[4][kScanThreads];
-  __shared__ unsigned long long wbest[2][kScanThreads / 32];
+  __shared__ int qlist[kQB];
   const int tid = threadIdx.x;
 
   for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
@@ -315,13 +325,6 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
     }
     __syncthreads();
 
-    // ---- the discords whose group holds this stream, two per pass over the chunk ----
-    auto active = [&](int r) {
-      const int64_t sr = static_cast<int64_t>(s) * a.K + r;
-      if (a.qinfo[sr * a.d + j].z == 0.f) return false;
-      const int i_star = a.idx[sr];
-      return !(t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl);
-    };
     // this thread's 8 windows: statistics once per item (vector loads)
     const int w0 = tid * kWinPerThread;
     float winv[kWinPerThread], wmean[kWinPerThread];
@@ -335,66 +338,72 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
       wmean[0] = m0.x; wmean[1] = m0.y; wmean[2] = m0.z; wmean[3] = m0.w;
       wmean[4] = m1.x; wmean[5] = m1.y; wmean[6] = m1.z; wmean[7] = m1.w;
     }
+
+    // ---- the discords whose group holds this stream: up to kQB of them staged at
+    // once (two per slot, interleaved for paired FMAs); then every warp runs its
+    // 256 windows through them on its own and merges with one atomic per query
     int r = 0;
     for (;;) {
-      int ra = -1, rb = -1;
-      for (; r < a.K && ra < 0; ++r)
-        if (active(r)) ra = r;
-      if (ra < 0) break;
-      for (; r < a.K && rb < 0; ++r)
-        if (active(r)) rb = r;
-      const int nq = rb >= 0 ? 2 : 1;
-      if (nq == 1) {  // one query, contiguous
-        const float* qg = a.Q + ((static_cast<int64_t>(s) * a.K + ra) * a.d + j) * m4;
-        for (int t = tid; t < m4; t += kScanThreads) qs[t] = qg[t];
-      } else {        // two queries, interleaved (q0_k, q1_k)
-        const float* qa = a.Q + ((static_cast<int64_t>(s) * a.K + ra) * a.d + j) * m4;
-        const float* qb = a.Q + ((static_cast<int64_t>(s) * a.K + rb) * a.d + j) * m4;
-        for (int t = tid; t < m4; t += kScanThreads) *reinterpret_cast<float2*>(qs + 2 * t) = make_float2(qa[t], qb[t]);
+      // next batch of active discords (the same list on every thread)
+      int nb = 0;
+      for (; r < a.K && nb < qb; ++r) {
+        const int64_t sr = static_cast<int64_t>(s) * a.K + r;
+        if (a.qinfo[sr * a.d + j].z == 0.f) continue;
+        const int i_star = a.idx[sr];
+        if (t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl) continue;
+        if (tid == 0) qlist[nb] = r;
+        ++nb;
       }
-      __syncthreads();
-      float acc[2][kWinPerThread];
-      if (nq == 2)
-        dot_windows<2>(xs, qs, m4, w0, acc);
-      else
-        dot_windows<1>(xs, qs, m4, w0, acc);
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (q < nq) {
-          const int64_t sr = static_cast<int64_t>(s) * a.K + (q == 0 ? ra : rb);
-          const float4 qi = a.qinfo[sr * a.d + j];
-          const int i_star = a.idx[sr];
-          unsigned long long best = 0ull;
-#pragma unroll
-          for (int u = 0; u < kWinPerThread; ++u) {
-            const int w = w0 + u;
-            const int t = t0 + w;
-            if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
-            const float inv_t = winv[u];
-            float key;
-            if (qi.w != 0.f) key = (inv_t == 0.f) ? 0.0f : -0.5f;  // rho 1 (dist 0) to a constant window, else 1/2
-            else if (inv_t == 0.f) key = -0.5f;                     // rho 1/2: 2m(1 - 1/2) = m
-            else {
-              const float cov = __fmaf_rn(-wmean[u], qi.y, acc[q][u]);
-              key = fminf(0.0f, fmaxf(-2.0f, __fmaf_rn(cov * qi.x, inv_t, -1.0f)));  // rho - 1
-            }
-            best = umax64(best, tsk_pack(key, t));
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
-          if ((tid & 31) == 0) wbest[q][tid >> 5] = best;
+      if (nb == 0) break;
+      __syncthreads();  // qlist written; the previous batch's queries no longer read
+      for (int b = 0; b < nb; b += 2) {
+        float* qs = qbuf + b * m4;  // slot b / 2: 2 * m4 floats
+        const float* qa = a.Q + ((static_cast<int64_t>(s) * a.K + qlist[b]) * a.d + j) * m4;
+        if (b + 1 < nb) {
+          const float* qb = a.Q + ((static_cast<int64_t>(s) * a.K + qlist[b + 1]) * a.d + j) * m4;
+          for (int t = tid; t < m4; t += kScanThreads) *reinterpret_cast<float2*>(qs + 2 * t) = make_float2(qa[t], qb[t]);
+        } else {
+          for (int t = tid; t < m4; t += kScanThreads) qs[t] = qa[t];
         }
       }
       __syncthreads();
-      if (tid < nq) {
-        unsigned long long b = 0ull;
+      for (int b = 0; b < nb; b += 2) {
+        const int nq = (b + 1 < nb) ? 2 : 1;
+        float acc[2][kWinPerThread];
+        if (nq == 2)
+          dot_windows<2>(xs, qbuf + b * m4, m4, w0, acc);
+        else
+          dot_windows<1>(xs, qbuf + b * m4, m4, w0, acc);
 #pragma unroll
-        for (int w = 0; w < kScanThreads / 32; ++w) b = umax64(b, wbest[tid][w]);
-        const int64_t sr = static_cast<int64_t>(s) * a.K + (tid == 0 ? ra : rb);
-        if (b) atomicMax(&a.best[sr * a.d + j], b);
+        for (int q = 0; q < 2; ++q) {
+          if (q < nq) {
+            const int64_t sr = static_cast<int64_t>(s) * a.K + qlist[b + q];
+            const float4 qi = a.qinfo[sr * a.d + j];
+            const int i_star = a.idx[sr];
+            unsigned long long best = 0ull;
+#pragma unroll
+            for (int u = 0; u < kWinPerThread; ++u) {
+              const int w = w0 + u;
+              const int t = t0 + w;
+              if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
+              const float inv_t = winv[u];
+              float key;
+              if (qi.w != 0.f) key = (inv_t == 0.f) ? 0.0f : -0.5f;  // rho 1 (dist 0) to a constant window, else 1/2
+              else if (inv_t == 0.f) key = -0.5f;                     // rho 1/2: 2m(1 - 1/2) = m
+              else {
+                const float cov = __fmaf_rn(-wmean[u], qi.y, acc[q][u]);
+                key = fminf(0.0f, fmaxf(-2.0f, __fmaf_rn(cov * qi.x, inv_t, -1.0f)));  // rho - 1
+              }
+              best = umax64(best, tsk_pack(key, t));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
+            if ((tid & 31) == 0 && best) atomicMax(&a.best[sr * a.d + j], best);
+          }
+        }
       }
-      __syncthreads();  // qs and wbest are reused by the next pass
     }
+    __syncthreads();  // shared buffers are reused by the next item
   }
 }
 
@@ -550,7 +559,8 @@ size_t scan_smem_bytes(int m) {
   const int m4 = (m + 3) & ~3;
   const int ns_max = kTW + m4 + 8;
   const size_t xs_words = static_cast<size_t>(ns_max) + 8;
-  return (xs_words + 2 * static_cast<size_t>(m4) + 2 * static_cast<size_t>(kTW) + 4 * static_cast<size_t>(kTW + m)) *
+  return (xs_words + static_cast<size_t>(query_batch(m)) * m4 + 2 * static_cast<size_t>(kTW) +
+          4 * static_cast<size_t>(kTW + m)) *
          sizeof(float);
 }
 
