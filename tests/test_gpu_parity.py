@@ -113,6 +113,26 @@ def test_degenerate_lengths(tsk):
         check_profile(x.astype(np.float64), m, 4, P[:l], I[:l])
 
 
+@pytest.mark.parametrize("case", ["offset", "long_m", "m2"])
+def test_offsets_long_and_shortest_subsequences(tsk, case):
+    """A large offset under a small spread (float32 anchors and statistics must not cancel),
+    a long subsequence (m = 1000: long anchors, several bands), and the shortest one (m = 2)."""
+    rng = np.random.default_rng(107)
+    if case == "offset":
+        m, excl = 64, 16
+        xs = [(2.5e4 + np.cumsum(rng.normal(size=n))).astype(np.float32) for n in (3000, 1700)]
+    elif case == "long_m":
+        m, excl = 1000, 250
+        xs = [np.cumsum(rng.normal(size=n)).astype(np.float32) for n in (6000, 2600)]
+    else:
+        m, excl = 2, 1
+        xs = [rng.normal(size=n).astype(np.float32) for n in (1500, 700)]
+    res = _streams(tsk, xs, m, excl)
+    for x, (P, I) in zip(xs, res):
+        l = len(x) - m + 1
+        check_profile(x.astype(np.float64), m, excl, P[:l], I[:l], rows=np.arange(0, l, 3))
+
+
 def test_stream_mask_leaves_masked_outputs_untouched(tsk):
     m = 32
     rng = np.random.default_rng(106)
