@@ -78,10 +78,10 @@ __global__ void __launch_bounds__(kStatThreads) k_colstats(const TIn* __restrict
 __device__ __forceinline__ double tsk_tbar(double x, double mu, double rinv) { return (x - mu) * rinv; }
 
 // Per-stream constants of the float32 fast path: mu = muh + mul, 1/sigma ~ rh,
-// and the absolute part of the error bound.
+// and the two coefficients of its safety threshold.
 struct NormC {
   double mu, r;   // float64 mean and 1/sigma (the reference)
-  float muh, mul, rh, babs;
+  float muh, mul, rh, t1, t2;
 };
 __device__ __forceinline__ NormC make_normc(double mu, double r) {
   NormC c;
@@ -90,28 +90,27 @@ __device__ __forceinline__ NormC make_normc(double mu, double r) {
   c.muh = static_cast<float>(mu);
   c.mul = static_cast<float>(mu - static_cast<double>(c.muh));
   c.rh = static_cast<float>(r);
-  c.babs = static_cast<float>(0x1p-45 * r * fabs(mu));
+  c.t1 = static_cast<float>(0x1p-21 * r * fabs(mu)) * 1.0001f;  // rounded up
+  c.t2 = static_cast<float>(0x1p-21 * r) * 1.0001f;
   return c;
 }
 
 // bfloat16 of the float64 value (x - mu) * r, computed without float64 in almost
 // all cases.  v = ((x - muh) - mul) * rh in float32 differs from the float64
-// value by at most 2^-21 |v| + 2^-45 r (|mu| + |x|) (four float32 roundings
-// plus the two-term mean's residual); when v is farther than that from every
-// bfloat16 rounding midpoint its round-to-nearest-even is the float64 value's,
-// otherwise (about 1e-4 of elements) the float64 value is formed and rounded.
+// value by at most E = 2^-21 |v| + A, A = 2^-45 r (|mu| + |x|) (four float32
+// roundings plus the two-term mean's residual).  A float32 ulp of a normal v
+// exceeds 2^-24 |v|, so where |v| >= 2^24 A = t1 + t2 |x| the error is below 9
+// ulps of v; if v's low 16 bits are then at least 10 ulps from the bfloat16
+// rounding midpoint (0x8000), no midpoint lies between v and the float64 value
+// and both round (nearest, ties to even) to the same bfloat16.  Otherwise
+// (about 1e-3 of elements) the float64 value is formed and rounded.
 __device__ __forceinline__ uint16_t tbar_bf16(float x, const NormC& c) {
   const float v = __fmul_rn(__fsub_rn(__fsub_rn(x, c.muh), c.mul), c.rh);
+  const float thr = fmaxf(__fmaf_rn(c.t2, fabsf(x), c.t1), 0x1p-100f);
   const uint32_t bits = __float_as_uint(v);
-  const int ex = static_cast<int>((bits >> 23) & 0xffu);
-  if (ex >= 40 && ex < 255) {
-    const float ulp = __uint_as_float(static_cast<uint32_t>(ex - 23) << 23);
-    const int dist = abs(static_cast<int>(bits & 0xffffu) - 0x8000);
-    const float bound = __fmaf_rn(0x1p-21f, fabsf(v), c.babs + 0x1p-45f * c.rh * fabsf(x));
-    if (static_cast<float>(dist - 1) * ulp > bound) {
-      const uint32_t rnd = 0x7fffu + ((bits >> 16) & 1u);
-      return static_cast<uint16_t>((bits + rnd) >> 16);
-    }
+  if (fabsf(v) >= thr && ((bits & 0xffffu) - 0x7ff6u) > 20u) {  // low 16 bits outside 0x8000 +- 10
+    const uint32_t rnd = 0x7fffu + ((bits >> 16) & 1u);
+    return static_cast<uint16_t>((bits + rnd) >> 16);
   }
   return tsk_f64_to_bf16_bits(tsk_tbar(static_cast<double>(x), c.mu, c.r));
 }
