@@ -52,8 +52,15 @@ constexpr int kVh = 8;                   // diagonals per lane in each half band
 constexpr int kHalf = 32 * kVh;          // 256 diagonals per half band
 constexpr int kBand = 2 * kHalf;         // 512 diagonals per warp band
 constexpr int kChunk = 32;               // rows between row flushes / ring refills
-constexpr int kRingEntries = 384;        // column ring entries of (half a, half b) pairs (multiple of 128)
+constexpr int kRingEntries = 320;        // column ring entries of (half a, half b) pairs
+constexpr int kRingPhys = kRingEntries + kRingEntries / 8;  // with one pad slot per 8 entries
 constexpr int kRingInit = 288;           // entries filled before the first row
+// During the chunk of steps [S0, S0 + 32) the lanes read ring entries [S0 + 8,
+// S0 + 288) while the copies for the next chunk write entries [S0 + 296,
+// S0 + 328); with 320 entries those land in slots of entries already consumed
+// (S0 + 7 and below), and the next chunk's reads (up to S0 + 319) are covered.
+static_assert(kVh + kRingInit >= kHalf + kChunk && kRingEntries >= kRingInit + kChunk && kRingEntries % kVh == 0,
+              "column ring too small for the refill distance");
 constexpr int kWarps = 4;                // warps per CTA
 constexpr int kMaxClaim = 16;            // work units a warp claims at once (at most)
 constexpr int kMaxWalk = 8192;           // rows walked from one anchor (at most)
@@ -240,8 +247,9 @@ __global__ void __launch_bounds__(kWinThreads) k_next_const(const int32_t* __res
 // precision near rho = 1, where close matches are told apart) with its 8 low
 // mantissa bits replaced by the diagonal's offset within its half (8t + v), so
 // maxima carry their argmax; the tag then costs at most 2^-16 of 1 - rho.
-// Column data (df, dg, 1/norm) stream through a swizzled shared-memory ring
+// Column data (df, dg, 1/norm) stream through a padded shared-memory ring
 // refilled 32 rows ahead; row data through a 32-row buffer of broadcast pairs.
+// Every per-row shared-memory access is a fixed offset from a per-block base.
 // ---------------------------------------------------------------------------
 struct MpArgs {
   const void* X;
@@ -260,10 +268,10 @@ struct MpArgs {
 };
 
 struct __align__(16) MpWarpSmem {
-  float2 ring[3][kRingEntries];  // column pairs (half a, half b), swizzled slots
-  float4 rrow[2][3][kChunk / 2]; // row broadcast pairs (v_s, v_s, v_s+1, v_s+1), double buffered
-  float2 rowbuf[kChunk][32];     // (row key half a, half b): [step][lane ^ (step & 15)]
-  float2 colbuf[kChunk];         // keys of the columns leaving lane 0, per step
+  float2 ring[3][kRingPhys];      // column pairs (half a, half b), slot ring_phys(entry)
+  float4 rrow[2][3][kChunk / 2];  // row broadcast pairs (v_s, v_s, v_s+1, v_s+1), double buffered
+  float2 rowbuf[32][kChunk + 1];  // (row key half a, half b): [lane][step], rows padded by one slot
+  float2 colbuf[kChunk];          // keys of the columns leaving lane 0, per step
 };
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
@@ -282,11 +290,12 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
   asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
   return r;
 }
-// ring slot (0 <= e < kRingEntries) -> physical 8-byte slot.  At a step the lanes
-// read entries e0 + 8t; XOR of the low three bits with bits 4..6 spreads the 16
-// lanes of a half warp over 16 distinct 8-byte bank pairs (the ring size is a
-// multiple of 128 entries, so the pattern continues across its wrap).
-__device__ __forceinline__ int ring_phys(int e) { return e ^ ((e >> 4) & 7); }
+// ring entry (0 <= e < kRingEntries) -> physical 8-byte slot: one pad slot after
+// every 8 entries.  A lane reads the 8 entries of an aligned block (one base plus
+// fixed offsets).  At a step the lanes read entries e0 + 8t, whose blocks start 9
+// slots apart, so the 16 lanes of a half warp fall on 16 distinct 8-byte bank
+// pairs unless their range wraps around the ring.
+__device__ __forceinline__ int ring_phys(int e) { return e + (e >> 3); }
 
 template <typename TX>
 __device__ __forceinline__ double ld_guard(const TX* __restrict__ x, int idx, int n) {
@@ -294,7 +303,7 @@ __device__ __forceinline__ double ld_guard(const TX* __restrict__ x, int idx, in
 }
 
 // Merge the 32 (or `count`) buffered rows and lane-0 column exits into the profile.
-// Buffer slot u belongs to row base + u and to columns base + u + d0 (+ 256).
+// Buffer step u belongs to row base + u and to columns base + u + d0 (+ 256).
 __device__ __forceinline__ void flush_chunk(MpWarpSmem& w, int count, int base, int d0, int l,
                                             unsigned long long* __restrict__ best,
                                             unsigned long long* __restrict__ bestc, int lane) {
@@ -302,10 +311,9 @@ __device__ __forceinline__ void flush_chunk(MpWarpSmem& w, int count, int base, 
   if (lane < count) {
     const int ir = base + lane;
     float ma = kEmpty, mb = kEmpty;
-    const int sw = lane & 15;
 #pragma unroll
-    for (int u = 0; u < 32; u += 2) {
-      const float2 q0 = w.rowbuf[lane][u ^ sw], q1 = w.rowbuf[lane][(u + 1) ^ sw];
+    for (int u = 0; u < 32; u += 2) {  // row `lane` of the chunk, from every source lane u
+      const float2 q0 = w.rowbuf[u][lane], q1 = w.rowbuf[u + 1][lane];
       ma = max3f(ma, q0.x, q1.x);
       mb = max3f(mb, q0.y, q1.y);
     }
@@ -477,7 +485,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
   }
 
   const int nsteps = MASKED ? ((rEnd - r0 + kChunk - 1) / kChunk) * kChunk : (rEnd - r0);
-  int ering = (kVh * (lane + 1)) % kRingEntries;  // ring slot of the column entering at step 0
+  int ering = (kVh * (lane + 1)) % kRingEntries;  // ring entry of the column entering at step 0
   for (int S0 = 0; S0 < nsteps; S0 += kChunk) {
     const int buf = (S0 / kChunk) & 1;
     // copies issued one chunk ago have landed; start those for the next chunk:
@@ -508,13 +516,11 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
     }
 #pragma unroll 1
     for (int sb = 0; sb < kChunk; sb += kVh) {  // 8-row blocks: one period of the slot rotation
-    // in a block the entering columns use ring slots ering .. ering + 7 (ering is a
-    // multiple of 8, so the swizzle is a fixed XOR: slot ering + (sr ^ rx))
-    const float2* ringb = &w.ring[0][ering];
-    const int rx = (ering >> 4) & 7;
+    // in a block the entering columns are ring entries ering .. ering + 7 (ering is
+    // a multiple of 8): consecutive slots from ring_phys(ering)
+    const float2* ringb = &w.ring[0][ring_phys(ering)];
     ering = (ering + kVh == kRingEntries) ? 0 : ering + kVh;
-    float2* rowp = &w.rowbuf[sb][0];
-    const int lx = lane ^ (sb & 8);  // row-buffer swizzle: lane ^ (step & 15) = lx ^ sr
+    float2* rowp = &w.rowbuf[lane][sb];
     // keys of one row (slot c = (v + sr) % 8 holds the column of diagonal v), with
     // the covariance advanced to the next row
     auto row_keys = [&](int sr, int i, float2 rdf2, float2 rdg2, float2 rinv2, float (&kA)[kVh],
@@ -538,7 +544,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
       }
       const float rka = fmaxf(max3f(max3f(max3f(kA[0], kA[1], kA[2]), kA[3], kA[4]), kA[5], kA[6]), kA[7]);
       const float rkb = fmaxf(max3f(max3f(max3f(kB[0], kB[1], kB[2]), kB[3], kB[4]), kB[5], kB[6]), kB[7]);
-      rowp[sr * 32 + (lx ^ sr)] = make_float2(rka, rkb);
+      rowp[sr] = make_float2(rka, rkb);
     };
     // the column in slot c0 leaves the lane (to lane - 1; lane 0's is complete for
     // this band) and the column entering from the ring takes its place
@@ -548,10 +554,9 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
       if (lane == 0) w.colbuf[s] = make_float2(la, lb);
       ckA[sr] = (lane == 31) ? kEmpty : ia;
       ckB[sr] = (lane == 31) ? kEmpty : ib;
-      const int o = sr ^ rx;
-      cdf2[sr] = ringb[o];
-      cdg2[sr] = ringb[kRingEntries + o];
-      cinv2[sr] = ringb[2 * kRingEntries + o];
+      cdf2[sr] = ringb[sr];
+      cdg2[sr] = ringb[kRingPhys + sr];
+      cinv2[sr] = ringb[2 * kRingPhys + sr];
     };
 #pragma unroll
     for (int gg = 0; gg < kVh / 2; ++gg) {
