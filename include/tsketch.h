@@ -55,7 +55,7 @@ enum {
   TSK_ERR_CUDA = 2,         /* a CUDA runtime call failed (message has the CUDA error) */
   TSK_ERR_OOM = 3,          /* workspace could not grow                                */
   TSK_ERR_UNSUPPORTED = 4,  /* valid request outside what this build implements        */
-  TSK_ERR_TIMEOUT = 5,      /* tsk_sync deadline passed before the stream drained      */
+  TSK_ERR_TIMEOUT = 5,      /* tsk_sync deadline passed, or a device-side wait gave up */
   TSK_ERR_NONFINITE = 6     /* a kernel met NaN/Inf in its input                        */
 };
 
@@ -99,7 +99,9 @@ TSK_API tsk_status tsk_mp_workspace_bytes(tsk_ctx* ctx, int32_t n_streams, const
                                           int32_t m, size_t* bytes_out);
 /* Wait until the stream drains, at most timeout_s seconds (<= 0: no limit),
  * then read and clear the device error word.  TSK_ERR_TIMEOUT if the deadline
- * passed (the work keeps running; call again). */
+ * passed (the work keeps running; call again), or if a kernel's bounded wait
+ * for its own asynchronous copies ran out (about a second; the results of the
+ * calls since the last sync are then invalid). */
 TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s);
 /* Rows per matrix-profile work unit (a band of 512 diagonals x `rows` rows):
  * 0 = automatic (about 64 units per resident warp, 2048..8192), else a

@@ -551,6 +551,7 @@ extern "C" TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s) {
   if (flag) {
     TSK_CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
     if (flag & TSK_DEVERR_NONFINITE) return tsk_fail(ctx, TSK_ERR_NONFINITE, "non-finite value in an input series");
+    if (flag & TSK_DEVERR_TIMEOUT) return tsk_fail(ctx, TSK_ERR_TIMEOUT, "a device-side wait gave up (results invalid)");
   }
   return TSK_OK;
 }

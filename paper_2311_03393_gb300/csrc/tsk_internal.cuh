@@ -12,7 +12,7 @@
 #define TSK_FULL_MASK 0xffffffffu
 
 // Error-word bits set by kernels (read by tsk_sync).
-enum : int { TSK_DEVERR_NONFINITE = 1 };
+enum : int { TSK_DEVERR_NONFINITE = 1, TSK_DEVERR_TIMEOUT = 2 };
 
 // ---------------------------------------------------------------------------
 // Context

@@ -8,8 +8,12 @@
 #include "tsk_internal.cuh"
 #include "tsk_ff.cuh"
 
+#include <cuda.h>  // CUtensorMap and the encoder's signature (the encoder is fetched from the driver at run time)
+
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 
 namespace {
@@ -77,73 +81,126 @@ __global__ void __launch_bounds__(kStatThreads) k_colstats(const TIn* __restrict
 // Normalised element in float64: (x - mu) / sigma, 0 for a constant stream.
 __device__ __forceinline__ double tsk_tbar(double x, double mu, double rinv) { return (x - mu) * rinv; }
 
-// Per-stream constants of the float32 fast path: mu = muh + mul, 1/sigma ~ rh,
-// and the two coefficients of its safety threshold.
+// Per-stream constants of the float32 fast path: v = ((x + nmuh) + nmul) * rh
+// approximates the float64 value (x - mu) * r, and c0 is the absolute part of
+// the bound on their difference.
 struct NormC {
-  double mu, r;   // float64 mean and 1/sigma (the reference)
-  float muh, mul, rh, t1, t2;
+  double mu, r;               // float64 mean and 1/sigma (the reference)
+  float nmuh, nmul, rh, c0;   // -float(mu), -float(mu - float(mu)), float(r), absolute error term
 };
 __device__ __forceinline__ NormC make_normc(double mu, double r) {
   NormC c;
   c.mu = mu;
   c.r = r;
-  c.muh = static_cast<float>(mu);
-  c.mul = static_cast<float>(mu - static_cast<double>(c.muh));
-  c.rh = static_cast<float>(r);
-  c.t1 = static_cast<float>(0x1p-21 * r * fabs(mu)) * 1.0001f;  // rounded up
-  c.t2 = static_cast<float>(0x1p-21 * r) * 1.0001f;
+  if (fabs(mu) < 1e37 && r < 1e37) {
+    const float muh = static_cast<float>(mu);
+    c.nmuh = -muh;
+    c.nmul = -static_cast<float>(mu - static_cast<double>(muh));
+    c.rh = static_cast<float>(r);
+    // r = 0 (a constant stream): v = 0 = w exactly
+    c.c0 = r > 0.0 ? static_cast<float>((0x1p-46 * r * fabs(mu) + 0x1p-125) * 1.001) : 0.f;
+  } else {  // out of the float32 path's range: every element takes the float64 path
+    c.nmuh = c.nmul = c.rh = 0.f;
+    c.c0 = INFINITY;
+  }
   return c;
 }
 
-// bfloat16 of the float64 value (x - mu) * r, computed without float64 in almost
-// all cases.  v = ((x - muh) - mul) * rh in float32 differs from the float64
-// value by at most E = 2^-21 |v| + A, A = 2^-45 r (|mu| + |x|) (four float32
-// roundings plus the two-term mean's residual).  A float32 ulp of a normal v
-// exceeds 2^-24 |v|, so where |v| >= 2^24 A = t1 + t2 |x| the error is below 9
-// ulps of v; if v's low 16 bits are then at least 10 ulps from the bfloat16
-// rounding midpoint (0x8000), no midpoint lies between v and the float64 value
-// and both round (nearest, ties to even) to the same bfloat16.  Otherwise
-// (about 1e-3 of elements) the float64 value is formed and rounded.
+// Packed bfloat16 pair, round to nearest even: element lo in bits 0..15, hi in 16..31.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// bfloat16 (nearest even) of the float64 value w = (x - mu) * r, with float64
+// arithmetic only where float32 cannot decide it.  The float32 value v (four
+// roundings, mu split in two floats) satisfies |v - w| <= 2^-22 |v| + 2^-47 r |mu|
+// (plus 2^-148 near the subnormal range); E = 2^-21 |v| + c0 bounds that with
+// a factor 2 to spare.  Rounding is monotone, so if v - E (rounded down) and
+// v + E (rounded up) have the same bfloat16, w has it too.  Otherwise (about
+// 2e-4 of elements) w is formed in float64 and rounded.
 __device__ __forceinline__ uint16_t tbar_bf16(float x, const NormC& c) {
-  const float v = __fmul_rn(__fsub_rn(__fsub_rn(x, c.muh), c.mul), c.rh);
-  const float thr = fmaxf(__fmaf_rn(c.t2, fabsf(x), c.t1), 0x1p-100f);
-  const uint32_t bits = __float_as_uint(v);
-  if (fabsf(v) >= thr && ((bits & 0xffffu) - 0x7ff6u) > 20u) {  // low 16 bits outside 0x8000 +- 10
-    const uint32_t rnd = 0x7fffu + ((bits >> 16) & 1u);
-    return static_cast<uint16_t>((bits + rnd) >> 16);
-  }
+  const float v = __fmul_rn(__fadd_rn(__fadd_rn(x, c.nmuh), c.nmul), c.rh);
+  const float e = __fmaf_rn(fabsf(v), 0x1p-21f, c.c0);
+  const uint32_t b = cvt_bf16x2(__fsub_rd(v, e), __fadd_ru(v, e));
+  if ((b & 0xffffu) == (b >> 16)) return static_cast<uint16_t>(b & 0xffffu);
   return tsk_f64_to_bf16_bits(tsk_tbar(static_cast<double>(x), c.mu, c.r));
 }
 __device__ __forceinline__ uint16_t tbar_bf16(double x, const NormC& c) {
   return tsk_f64_to_bf16_bits(tsk_tbar(x, c.mu, c.r));
 }
+// The same for two samples of one stream, packed (x0 in the low half); the
+// float32 steps run on pairs.
+// The float32 part has no branch (ok = false where float64 must decide), so a
+// caller can run several pairs side by side and fix the rare ones afterwards.
+__device__ __forceinline__ uint32_t tbar_bf16x2_fast(float x0, float x1, float2 nmuh2, float2 nmul2, float2 rh2, float c0,
+                                                     bool& ok) {
+  const float2 v = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(x0, x1), nmuh2), nmul2), rh2);
+  const float2 e = make_float2(__fmaf_rn(fabsf(v.x), 0x1p-21f, c0), __fmaf_rn(fabsf(v.y), 0x1p-21f, c0));
+  const float2 lo = __ffma2_rd(e, make_float2(-1.f, -1.f), v);
+  const float2 hi = __fadd2_ru(v, e);
+  const uint32_t blo = cvt_bf16x2(lo.x, lo.y);
+  ok = blo == cvt_bf16x2(hi.x, hi.y);
+  return blo;
+}
+__device__ __forceinline__ uint32_t tbar_bf16x2_f64(double x0, double x1, const NormC* __restrict__ nc) {
+  const double mu = nc->mu, r = nc->r;
+  return static_cast<uint32_t>(tsk_f64_to_bf16_bits(tsk_tbar(x0, mu, r))) |
+         (static_cast<uint32_t>(tsk_f64_to_bf16_bits(tsk_tbar(x1, mu, r))) << 16);
+}
 
 // ---------------------------------------------------------------------------
 // bfloat16 tensor-core sketch.
 //
-// k_sketch_prep turns R into bfloat16 bits, transposed and zero-padded
-// (Rt[g][j], kp x dp), and the per-stream statistics into NormC constants, once
-// per call.  k_sketch_bf16: one CTA = 64 time points x 64 outputs (blockIdx.y
-// picks the group of 64 outputs) x one range of dimensions (blockIdx.z, when
-// the grid would otherwise leave SMs idle); 4 warps, one m16 tile of time
-// points each, up to 8 n8 tiles; dimensions in stages of 32, the next stage's
-// samples loaded into registers while the current stage's MMAs run.  With
-// several dimension ranges the partial sums go to a workspace and
-// k_sketch_reduce adds them in a fixed order (deterministic).
+// k_sketch_prep turns R into bfloat16 MMA B fragments, in the order the warps
+// read them (per stage of 32 dimensions, n8 output tile and lane: one 16-byte
+// word holding the lane's fragments of both k16 steps), zero past d and k, and
+// the per-stream statistics into NormC constants, once per call.
+//
+// k_sketch_bf16: a CTA of 4 warps covers 16 x (4 / wd) time points of one
+// series, one group of up to 64 outputs (blockIdx.y) and one range of
+// dimensions (blockIdx.z, only when the grid would otherwise leave SMs idle);
+// its warps split the range into wd parts (wd = 4 for d >= 256, so a CTA is one
+// m16 tile of time points and the grid has many small CTAs).  Each warp runs
+// independently over its dimensions in stages of 32: lane j loads 16
+// consecutive samples of dimension j (16-byte loads where aligned) two stages
+// ahead, converts them in pairs with one set of normalisation constants and
+// writes them with two 16-byte stores into the warp's [dimension][time] tile;
+// the A fragments come from that tile with ldmatrix.trans, no block barrier.
+// The wd partial sums of a time tile are added in a fixed order at the end,
+// and with several dimension ranges k_sketch_reduce adds those in a fixed
+// order (deterministic).
 // ---------------------------------------------------------------------------
-constexpr int kSkT = 64;       // time points per CTA
+constexpr int kSkBlock = 64;       // time points per block of the batch layout
 constexpr int kSkThreads = 128;
-constexpr int kSkKC = 32;      // dimensions per stage
-constexpr int kSkRow = kSkKC + 8;  // padded smem row (80 bytes: conflict-free fragment loads)
+constexpr int kSkWarps = kSkThreads / 32;
+constexpr int kSkKC = 32;          // dimensions per stage
+constexpr int kSkArow = 16 + 8;    // padded tile row: 16 time points (48 bytes: conflict-free stores and ldmatrix rows)
 
-__global__ void k_sketch_prep(const float* __restrict__ R, int32_t d, int32_t k, int32_t dp, int32_t kp,
-                              const double* __restrict__ stats, int64_t nstreams, uint16_t* __restrict__ Rt,
+// dimension parts per CTA (warps splitting the dimensions) for d dimensions
+__host__ __device__ inline int sketch_wd(int32_t d) { return d >= 256 ? 4 : (d >= 64 ? 2 : 1); }
+
+__device__ __forceinline__ uint32_t pack_bf16_pair(uint16_t lo, uint16_t hi) {
+  return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
+__global__ void k_sketch_prep(const float* __restrict__ R, int32_t d, int32_t k, int32_t nstage, int32_t kp,
+                              const double* __restrict__ stats, int64_t nstreams, uint4* __restrict__ Rf,
                               NormC* __restrict__ nc) {
   const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t nr = static_cast<int64_t>(kp) * dp;
+  const int64_t nr = static_cast<int64_t>(nstage) * (kp / 8) * 32;
   if (e < nr) {
-    const int g = static_cast<int>(e / dp), j = static_cast<int>(e % dp);
-    Rt[e] = (g < k && j < d) ? tsk_f64_to_bf16_bits(static_cast<double>(R[static_cast<int64_t>(j) * k + g])) : 0;
+    const int lane = static_cast<int>(e & 31);
+    const int64_t w = e >> 5;
+    const int g8 = static_cast<int>(w % (kp / 8)), q = static_cast<int>(w / (kp / 8));
+    const int g = g8 * 8 + (lane >> 2), j0 = q * kSkKC + 2 * (lane & 3);
+    auto rb = [&](int j) -> uint16_t {
+      return (g < k && j < d) ? tsk_f64_to_bf16_bits(static_cast<double>(R[static_cast<int64_t>(j) * k + g])) : 0;
+    };
+    // b0 = (k 2t, 2t+1), b1 = (k 2t+8, 2t+9) of the k16 steps at 0 and 16
+    Rf[e] = make_uint4(pack_bf16_pair(rb(j0), rb(j0 + 1)), pack_bf16_pair(rb(j0 + 8), rb(j0 + 9)),
+                       pack_bf16_pair(rb(j0 + 16), rb(j0 + 17)), pack_bf16_pair(rb(j0 + 24), rb(j0 + 25)));
   }
   if (e < nstreams) {
     const double mu = stats[2 * e], sg = stats[2 * e + 1];
@@ -151,111 +208,341 @@ __global__ void k_sketch_prep(const float* __restrict__ R, int32_t d, int32_t k,
   }
 }
 
-template <typename TIn, int NTM>
-__global__ void __launch_bounds__(kSkThreads, (NTM <= 4 ? 6 : 4)) k_sketch_bf16(const TIn* __restrict__ T, const int64_t* __restrict__ cum,
-                                                           const int32_t* __restrict__ len,
-                                                           const int64_t* __restrict__ blk_prefix, int32_t n_series,
-                                                           int32_t d, int32_t dchunk, const uint16_t* __restrict__ Rt,
-                                                           int32_t dp, int32_t k, const NormC* __restrict__ nc,
-                                                           float* __restrict__ S, int64_t part_stride) {
-  __shared__ __align__(16) uint16_t As[kSkT][kSkRow];
-  __shared__ __align__(16) uint16_t Bs[64][kSkRow];
-  __shared__ NormC snc[kSkKC];
+// 16 consecutive samples (a 16-byte aligned address, or guarded scalar loads)
+__device__ __forceinline__ void sk_load16(const float* __restrict__ p, int nv, bool vec, float (&x)[16]) {
+  if (vec) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(p) + u);
+      x[4 * u] = q.x;
+      x[4 * u + 1] = q.y;
+      x[4 * u + 2] = q.z;
+      x[4 * u + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = u < nv ? p[u] : 0.f;
+  }
+}
+__device__ __forceinline__ void sk_load16(const double* __restrict__ p, int nv, bool vec, double (&x)[16]) {
+  if (vec) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double2 q = __ldg(reinterpret_cast<const double2*>(p) + u);
+      x[2 * u] = q.x;
+      x[2 * u + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = u < nv ? p[u] : 0.0;
+  }
+}
 
-  const int s = tsk_find_segment<int64_t>(blk_prefix, n_series, static_cast<int64_t>(blockIdx.x));
-  const int n = len[s];
-  const int t0 = static_cast<int>(blockIdx.x - blk_prefix[s]) * kSkT;
-  const int64_t tbase = static_cast<int64_t>(d) * cum[s];
-  const int64_t sbase = static_cast<int64_t>(k) * cum[s] + static_cast<int64_t>(blockIdx.z) * part_stride;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gid = lane >> 2, tig = lane & 3;
-  const int gbase = static_cast<int>(blockIdx.y) * 64;
-  const int NT = min(NTM, (k - gbase + 7) >> 3);  // n8 tiles of this output group (NTM: at most)
-  const int jb = static_cast<int>(blockIdx.z) * dchunk;
-  const int je = min(d, jb + dchunk);
+// A work unit of the persistent sketch kernel, as seen by one warp: its 16
+// time points of one series, output group gy and dimensions [jb, je) (empty
+// when the time points lie past the series end).
+struct SkUnit {
+  int s, n, tw, nv, jb, je, gy;
+  int64_t tbase, sbase;
+};
 
-  float acc[NTM][4];
-#pragma unroll
-  for (int q = 0; q < NTM; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+constexpr int kSkSlots = 3;                      // stages of samples in flight per warp
+constexpr int kSkTileBytes = kSkKC * kSkArow * 2;
+// one stage: 32 dimensions x 16 samples
+__host__ __device__ constexpr int sk_slot_bytes(int elem) { return kSkKC * 16 * elem; }
+// dynamic shared memory: [slots: warps x kSkSlots stages][tiles: warps x 1.5 KB][partial sums][mbarriers]
+__host__ __device__ constexpr int sk_smem_bytes(int ntm, int elem) {
+  return kSkWarps * kSkSlots * sk_slot_bytes(elem) + kSkWarps * kSkTileBytes + 2 * kSkWarps * ntm * 4 * 32 * 4 +
+         kSkWarps * kSkSlots * 8;
+}
 
-  // this thread's share of a stage: 16 samples (dimension e >> 6, time e & 63 for
-  // e = tid + 128 u) and two 8-wide rows of R (output e2 >> 2, dimensions 8 (e2 & 3)..)
-  TIn xv[16];
-  uint4 rv[2];
-  auto load_stage = [&](int j0) {
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int e = tid + u * kSkThreads;
-      const int j = j0 + (e >> 6), t = t0 + (e & 63);
-      xv[u] = (j < je && t < n) ? T[tbase + static_cast<int64_t>(j) * n + t] : TIn(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e2 = tid + u * kSkThreads;
-      const int g = gbase + (e2 >> 2), jj = j0 + 8 * (e2 & 3);
-      rv[u] = *reinterpret_cast<const uint4*>(Rt + static_cast<int64_t>(g) * dp + jj);
-    }
-  };
-  load_stage(jb);
-  for (int j0 = jb; j0 < je; j0 += kSkKC) {
-    __syncthreads();  // the previous stage's fragments have been read
-    if (tid < kSkKC) snc[tid] = (j0 + tid < je) ? nc[static_cast<int64_t>(s) * d + j0 + tid] : make_normc(0.0, 0.0);
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int e = tid + u * kSkThreads;
-      const int jl = e >> 6, tl = e & 63;
-      As[tl][jl] = (j0 + jl < je && t0 + tl < n) ? tbar_bf16(xv[u], snc[jl]) : uint16_t(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e2 = tid + u * kSkThreads;
-      uint4 r = rv[u];
-      // dimensions past this range's end contribute nothing
-      const int jj = j0 + 8 * (e2 & 3);
-      if (jj + 8 > je) {
-        uint16_t* h = reinterpret_cast<uint16_t*>(&r);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (jj + q >= je) h[q] = 0;
-      }
-      *reinterpret_cast<uint4*>(&Bs[e2 >> 2][8 * (e2 & 3)]) = r;
-    }
-    __syncthreads();
-    if (j0 + kSkKC < je) load_stage(j0 + kSkKC);  // overlaps the MMAs below
-    const int r0 = warp * 16 + gid;
-#pragma unroll
-    for (int ks = 0; ks < kSkKC; ks += 16) {
-      const uint32_t a0 = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * tig]);
-      const uint32_t a1 = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * tig]);
-      const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * tig + 8]);
-      const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * tig + 8]);
-#pragma unroll
-      for (int nt = 0; nt < NTM; ++nt) {
-        if (nt < NT) {
-          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][ks + 2 * tig]);
-          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[nt * 8 + gid][ks + 2 * tig + 8]);
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-              : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-        }
-      }
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the barrier's phase `parity` to complete, at most ~1 s (then flag a
+// timeout in the error word and return: the data are not valid).
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1LL << 31)) {
+      atomicOr(err, TSK_DEVERR_TIMEOUT);
+      return;
     }
   }
-#pragma unroll
-  for (int nt = 0; nt < NTM; ++nt) {
-    if (nt < NT) {
-      const int g = gbase + nt * 8 + 2 * tig;
-      const int t = t0 + warp * 16 + gid;
-      if (t < n) {
-        if (g < k) S[sbase + static_cast<int64_t>(g) * n + t] = acc[nt][0];
-        if (g + 1 < k) S[sbase + static_cast<int64_t>(g + 1) * n + t] = acc[nt][1];
+}
+// 2-D tile (x: time, y: dimension) of the tensor map into shared memory, completing on bar
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// A stage slot holds row r (dimension j0 + r): float32 as 64 bytes at r * 64,
+// its 16-byte chunk c at chunk c ^ ((r >> 1) & 3) (the tensor map's 64-byte
+// swizzle; slots are 512-byte aligned); float64 as 128 bytes at r * 128, chunk c
+// at c ^ (r & 7).  Either way the 32 lanes reading their rows hit distinct banks.
+template <typename TIn>
+__device__ __forceinline__ int sk_chunk_off(int r, int c) {
+  return sizeof(TIn) == 4 ? r * 64 + ((c ^ ((r >> 1) & 3)) << 4) : r * 128 + ((c ^ (r & 7)) << 4);
+}
+
+template <typename TIn, int NTM>
+__global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ? 4 : 3)) k_sketch_bf16(
+    const __grid_constant__ CUtensorMap tmap, int use_tma, const TIn* __restrict__ T,
+    const int64_t* __restrict__ cum, const int32_t* __restrict__ len, const int64_t* __restrict__ blk_prefix,
+    int32_t n_series, int64_t n_ctiles, int32_t d, int32_t dchunk, int32_t parts, int32_t wd,
+    const uint4* __restrict__ Rf, int32_t kp, int32_t k, const NormC* __restrict__ nc, float* __restrict__ S,
+    int64_t part_stride, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sk_smem[];
+  constexpr int kSlotBytes = sk_slot_bytes(static_cast<int>(sizeof(TIn)));
+  constexpr int kChunks = static_cast<int>(sizeof(TIn));  // 16-byte chunks per row
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned char* slots = sk_smem + warp * (kSkSlots * kSlotBytes);
+  uint16_t(*tile)[kSkArow] =
+      reinterpret_cast<uint16_t(*)[kSkArow]>(sk_smem + kSkWarps * kSkSlots * kSlotBytes + warp * kSkTileBytes);
+  float(*red)[kSkWarps][NTM * 4][32] = reinterpret_cast<float(*)[kSkWarps][NTM * 4][32]>(
+      sk_smem + kSkWarps * kSkSlots * kSlotBytes + kSkWarps * kSkTileBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sk_smem + kSkWarps * kSkSlots * kSlotBytes + kSkWarps * kSkTileBytes +
+                                               2 * kSkWarps * NTM * 4 * 32 * 4) +
+                   warp * kSkSlots;
+
+  const int tsub = warp / wd, dpart = warp % wd;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int kgroups = kp / 64;
+  const int C = static_cast<int>(n_ctiles), G = static_cast<int>(gridDim.x);
+  const int wsh = wd == 4 ? 2 : (wd == 2 ? 1 : 0);
+
+  // the TMA path needs the 64-byte swizzle's 512-byte alignment of every slot
+  if ((smem_u32(sk_smem) & 1023u) != 0) use_tma = 0;
+  if (lane == 0) {
+    for (int i = 0; i < kSkSlots; ++i) mbar_init(&bars[i], 1);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  __syncwarp();
+
+  // unit u = c + C (gy + kgroups z): CTA tile c (wd per 64-point block, each
+  // 16 x (4 / wd) time points), output group gy, dimension range z.  A CTA
+  // walks u = blockIdx.x, + G, ... by updating (c, gy, z) in place.
+  auto first_unit = [&](int& c, int& gy, int& z) {
+    c = static_cast<int>(blockIdx.x);
+    gy = z = 0;
+    while (c >= C) {
+      c -= C;
+      if (++gy == kgroups) { gy = 0; ++z; }
+    }
+  };
+  auto next_unit = [&](int& c, int& gy, int& z) {
+    c += G;
+    while (c >= C) {
+      c -= C;
+      if (++gy == kgroups) { gy = 0; ++z; }
+    }
+  };
+  auto decode = [&](int c, int gy, int z, SkUnit& I) {
+    I.gy = gy;
+    const int blk = c >> wsh;
+    I.s = tsk_find_segment<int64_t>(blk_prefix, n_series, static_cast<int64_t>(blk));
+    I.n = len[I.s];
+    I.tw = (blk - static_cast<int>(blk_prefix[I.s])) * kSkBlock + (c & (wd - 1)) * (16 * (4 / wd)) + 16 * tsub;
+    I.nv = min(16, max(0, I.n - I.tw));
+    I.tbase = static_cast<int64_t>(d) * cum[I.s];
+    I.sbase = static_cast<int64_t>(k) * cum[I.s] + static_cast<int64_t>(z) * part_stride;
+    const int rb = z * dchunk, re = min(d, rb + dchunk);
+    const int wchunk = ((re - rb + wd - 1) / wd + kSkKC - 1) / kSkKC * kSkKC;
+    I.jb = min(re, rb + dpart * wchunk);
+    I.je = I.nv > 0 ? min(re, I.jb + wchunk) : I.jb;
+  };
+
+  // issue cursor: the next stage of this warp's stream to fetch (unit (pc, pg, pz), dimensions pj..)
+  int pc, pg, pz, pj = 0;
+  first_unit(pc, pg, pz);
+  SkUnit P{};
+  auto skip_empty = [&]() {
+    while (pz < parts && pj >= P.je) {
+      next_unit(pc, pg, pz);
+      if (pz < parts) {
+        decode(pc, pg, pz, P);
+        pj = P.jb;
       }
-      if (t + 8 < n) {
-        if (g < k) S[sbase + static_cast<int64_t>(g) * n + t + 8] = acc[nt][2];
-        if (g + 1 < k) S[sbase + static_cast<int64_t>(g + 1) * n + t + 8] = acc[nt][3];
+    }
+  };
+  if (pz < parts) {
+    decode(pc, pg, pz, P);
+    pj = P.jb;
+    skip_empty();
+  }
+  // fetch the cursor's stage into slot i: one TMA tile (rows past d and time
+  // points past n arrive as zeros), or, without a tensor map, each lane's row
+  // by plain loads; then advance the cursor
+  auto issue = [&](int i) {
+    if (pz >= parts) return;
+    unsigned char* slot = slots + i * kSlotBytes;
+    if (use_tma) {
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&bars[i], kSlotBytes);
+        tma_load_2d(slot, &tmap, P.tw, pj, &bars[i]);
+      }
+    } else {
+      const int j = pj + lane;
+      TIn x[16];
+      if (j < P.je) {
+        const TIn* src = T + P.tbase + static_cast<int64_t>(j) * P.n + P.tw;
+        sk_load16(src, P.nv, P.nv == 16 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0, x);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = TIn(0);
+      }
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c)
+        *reinterpret_cast<uint4*>(slot + sk_chunk_off<TIn>(lane, c)) = *reinterpret_cast<const uint4*>(&x[c * (16 / kChunks)]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[i]);
+    }
+    pj += kSkKC;
+    skip_empty();
+  };
+#pragma unroll
+  for (int i = 0; i < kSkSlots; ++i) issue(i);
+
+  float acc[NTM][4];
+  const int i8 = lane >> 3, r8 = lane & 7;  // ldmatrix: this lane's row of matrix i8
+  int kst = 0;  // ordinal of the next stage to process
+  int ord = 0;  // unit ordinal (parity picks the partial-sum buffer)
+  int uc, ug, uz;
+  first_unit(uc, ug, uz);
+  for (; uz < parts; next_unit(uc, ug, uz), ++ord) {
+    SkUnit I;
+    decode(uc, ug, uz, I);
+    const int NT = min(NTM, (k - I.gy * 64 + 7) >> 3);  // n8 tiles of this output group (NTM: at most)
+#pragma unroll
+    for (int q = 0; q < NTM; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+    for (int j0 = I.jb; j0 < I.je; j0 += kSkKC, ++kst) {
+      const int si = kst % kSkSlots;
+      const int j = j0 + lane;
+      const bool jv = j < I.je;
+      // constants of this lane's dimension and the stage's B fragments (both k16 steps)
+      const NormC* cp = nc + static_cast<int64_t>(I.s) * d + (jv ? j : I.jb);
+      const float4 cst = __ldg(reinterpret_cast<const float4*>(&cp->nmuh));
+      uint4 bf[NTM];
+      {
+        const uint4* base = Rf + (static_cast<int64_t>(j0 / kSkKC) * (kp / 8) + I.gy * 8) * 32 + lane;
+#pragma unroll
+        for (int nt = 0; nt < NTM; ++nt) bf[nt] = __ldg(base + nt * 32);
+      }
+      mbar_wait_bounded(&bars[si], static_cast<unsigned>((kst / kSkSlots) & 1), err);
+      TIn x[16];
+      {
+        const unsigned char* slot = slots + si * kSlotBytes;
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c)
+          *reinterpret_cast<uint4*>(&x[c * (16 / kChunks)]) = *reinterpret_cast<const uint4*>(slot + sk_chunk_off<TIn>(lane, c));
+      }
+      __syncwarp();  // every lane has read the slot: refill it with the stage kSkSlots ahead
+      if (use_tma && lane == 0) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(si);
+      uint32_t pk[8];
+      if constexpr (sizeof(TIn) == 4) {
+        const float2 nmuh2 = make_float2(cst.x, cst.x), nmul2 = make_float2(cst.y, cst.y), rh2 = make_float2(cst.z, cst.z);
+        unsigned redo = 0;  // pairs that float32 cannot decide (about 1 in 2500)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          bool ok;
+          pk[q] = tbar_bf16x2_fast(x[2 * q], x[2 * q + 1], nmuh2, nmul2, rh2, cst.w, ok);
+          redo |= ok ? 0u : (1u << q);
+        }
+        if (redo) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (redo & (1u << q)) pk[q] = tbar_bf16x2_f64(x[2 * q], x[2 * q + 1], cp);
+        }
+      } else {
+        const double mu = cp->mu, r = cp->r;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          pk[q] = pack_bf16_pair(tsk_f64_to_bf16_bits(tsk_tbar(x[2 * q], mu, r)), tsk_f64_to_bf16_bits(tsk_tbar(x[2 * q + 1], mu, r)));
+      }
+      if (!jv || I.nv < 16) {  // zero the samples past the series end or the warp's range end
+        const int lim = jv ? I.nv : 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) pk[q] = 2 * q >= lim ? 0u : (2 * q + 1 >= lim ? (pk[q] & 0xffffu) : pk[q]);
+      }
+      {
+        uint4* dst = reinterpret_cast<uint4*>(&tile[lane][0]);
+        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        // A fragments (16 time points x 16 dimensions), transposed from the tile
+        uint32_t a0, a1, a2, a3;
+        const unsigned addr = smem_u32(&tile[16 * ks + (i8 >> 1) * 8 + r8][(i8 & 1) * 8]);
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
+                     : "r"(addr));
+#pragma unroll
+        for (int nt = 0; nt < NTM; ++nt) {
+          if (nt < NT) {
+            const uint32_t b0 = ks ? bf[nt].z : bf[nt].x, b1 = ks ? bf[nt].w : bf[nt].y;
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+          }
+        }
+      }
+      __syncwarp();  // the tile's fragments have been read before the next stage's stores
+    }
+    if (wd > 1) {  // add the dimension parts of each time tile in part order
+      float(*rb)[NTM * 4][32] = red[ord & 1];
+#pragma unroll
+      for (int nt = 0; nt < NTM; ++nt)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) rb[warp][nt * 4 + c][lane] = acc[nt][c];
+      __syncthreads();  // also: every warp has finished reading the buffer of two units ago
+      if (dpart != 0) continue;
+#pragma unroll
+      for (int nt = 0; nt < NTM; ++nt)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float v = rb[warp][nt * 4 + c][lane];
+          for (int p = 1; p < wd; ++p) v += rb[warp + p][nt * 4 + c][lane];
+          acc[nt][c] = v;
+        }
+    }
+    if (I.nv <= 0) continue;
+#pragma unroll
+    for (int nt = 0; nt < NTM; ++nt) {
+      if (nt < NT) {
+        const int g = I.gy * 64 + nt * 8 + 2 * tig;
+        const int t = I.tw + gid;
+        if (t < I.n) {
+          if (g < k) S[I.sbase + static_cast<int64_t>(g) * I.n + t] = acc[nt][0];
+          if (g + 1 < k) S[I.sbase + static_cast<int64_t>(g + 1) * I.n + t] = acc[nt][1];
+        }
+        if (t + 8 < I.n) {
+          if (g < k) S[I.sbase + static_cast<int64_t>(g) * I.n + t + 8] = acc[nt][2];
+          if (g + 1 < k) S[I.sbase + static_cast<int64_t>(g + 1) * I.n + t + 8] = acc[nt][3];
+        }
       }
     }
   }
@@ -282,8 +569,8 @@ __global__ void __launch_bounds__(128) k_sketch_fma(const TIn* __restrict__ T, c
                                                     const double* __restrict__ stats, Acc* __restrict__ S) {
   const int s = tsk_find_segment<int64_t>(blk_prefix, n_series, static_cast<int64_t>(blockIdx.x));
   const int n = len[s];
-  const int t = static_cast<int>(blockIdx.x - blk_prefix[s]) * kSkT + static_cast<int>(threadIdx.x);
-  if (threadIdx.x >= kSkT || t >= n) return;
+  const int t = static_cast<int>(blockIdx.x - blk_prefix[s]) * kSkBlock + static_cast<int>(threadIdx.x);
+  if (threadIdx.x >= kSkBlock || t >= n) return;
   const int64_t tbase = static_cast<int64_t>(d) * cum[s];
   const int64_t sbase = static_cast<int64_t>(k) * cum[s];
   for (int g0 = 0; g0 < k; g0 += 8) {
@@ -407,10 +694,36 @@ tsk_status tsk_launch_colstats(tsk_ctx* ctx, const void* T, int t_dtype, const i
   return TSK_OK;
 }
 
+// Tensor map of one float32 series (d rows of n samples, row stride n * 4 bytes):
+// boxes of 16 samples x 32 rows, 64-byte swizzle, zero fill outside the series.
+// The encoder comes from the driver through the runtime (no link to libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static bool sketch_tensor_map(CUtensorMap* map, const void* T, int64_t n, int32_t d) {
+  static EncodeTiledFn encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<EncodeTiledFn>(fn);
+  });
+  if (!encode || n <= 0 || d <= 0) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(d)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(n) * 4};
+  const cuuint32_t box[2] = {16, kSkKC};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(T), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Dimension ranges of the bfloat16 sketch: enough CTAs to fill the GPU about 8
 // deep, each range at least 256 dimensions.
 static void sketch_split(int64_t total_blocks, int32_t d, int32_t k, int sm_count, int* nparts, int* dchunk) {
-  const int64_t tiles = total_blocks * ((k + 63) / 64);
+  const int64_t tiles = total_blocks * sketch_wd(d) * ((k + 63) / 64);
   const int64_t want = static_cast<int64_t>(sm_count) * 8;
   int p = static_cast<int>(std::min<int64_t>(std::max<int64_t>(1, (want + tiles - 1) / tiles), std::max(1, d / 256)));
   int c = (d + p - 1) / p;
@@ -424,9 +737,10 @@ size_t tsk_sketch_ws_bytes(int32_t n_series, int32_t d, int32_t k, int64_t total
                            int sm_count) {
   int p = 1, c = d;
   sketch_split(total_blocks, d, k, sm_count, &p, &c);
-  const size_t dp = (static_cast<size_t>(d) + kSkKC - 1) / kSkKC * kSkKC + kSkKC;
+  const size_t nstage = (static_cast<size_t>(d) + kSkKC - 1) / kSkKC;
   const size_t kp = (static_cast<size_t>(k) + 63) / 64 * 64;
-  size_t b = tsk_carver::bytes_for(kp * dp, 2) + tsk_carver::bytes_for(static_cast<size_t>(n_series) * d, sizeof(NormC));
+  size_t b = tsk_carver::bytes_for(nstage * (kp / 8) * 32, sizeof(uint4)) +
+             tsk_carver::bytes_for(static_cast<size_t>(n_series) * d, sizeof(NormC));
   if (p > 1) b += tsk_carver::bytes_for(static_cast<size_t>(p) * k * total_samples, 4);
   return b + 512;
 }
@@ -443,41 +757,60 @@ tsk_status tsk_launch_sketch(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n
   if (precision == TSK_SKETCH_BF16) {
     int parts = 1, dchunk = d;
     sketch_split(total_blocks, d, k, ctx->sm_count, &parts, &dchunk);
-    // the stage loop reads R rows 8 dimensions at a time up to one stage past a range
-    const int32_t dp = (d + kSkKC - 1) / kSkKC * kSkKC + kSkKC;
+    const int32_t nstage = (d + kSkKC - 1) / kSkKC;
     const int32_t kp = (k + 63) / 64 * 64;
+    const int32_t wd = sketch_wd(d);
     tsk_carver cv(ws);
-    uint16_t* Rt = cv.take<uint16_t>(static_cast<size_t>(kp) * dp);
+    const int64_t nfrag = static_cast<int64_t>(nstage) * (kp / 8) * 32;
+    uint4* Rf = cv.take<uint4>(static_cast<size_t>(nfrag));
     NormC* nc = cv.take<NormC>(static_cast<size_t>(n_series) * d);
     float* part = parts > 1 ? cv.take<float>(static_cast<size_t>(parts) * k * total_samples) : nullptr;
     const int64_t nstreams = static_cast<int64_t>(n_series) * d;
-    const int64_t nprep = std::max<int64_t>(static_cast<int64_t>(kp) * dp, nstreams);
-    k_sketch_prep<<<static_cast<unsigned>((nprep + 255) / 256), 256, 0, st>>>(R, d, k, dp, kp, stats, nstreams, Rt, nc);
+    const int64_t nprep = std::max<int64_t>(nfrag, nstreams);
+    k_sketch_prep<<<static_cast<unsigned>((nprep + 255) / 256), 256, 0, st>>>(R, d, k, nstage, kp, stats, nstreams, Rf, nc);
     TSK_LAUNCH_CHECK(ctx, "k_sketch_prep");
-    const dim3 grid_bf16(static_cast<unsigned>(total_blocks), static_cast<unsigned>(kp / 64),
-                         static_cast<unsigned>(parts));
+    const int64_t n_ctiles = total_blocks * wd;
+    const int64_t nunits = n_ctiles * (kp / 64) * parts;
+    if (nunits > 0x3fffffff) return tsk_fail(ctx, TSK_ERR_UNSUPPORTED, "batch too large for the sketch");
     float* out = parts > 1 ? part : static_cast<float*>(S);
     const int64_t pstride = static_cast<int64_t>(k) * total_samples;
     {
       // accumulator tiles per thread: as many n8 tiles as the widest output group needs
       const int nt = std::min(8, (k + 7) / 8);
       const int ntm = nt <= 1 ? 1 : nt <= 2 ? 2 : nt <= 4 ? 4 : 8;
+      // one float32 series whose rows are 16-byte aligned: stages come by TMA
+      CUtensorMap tmap;
+      std::memset(&tmap, 0, sizeof(tmap));
+      int use_tma = 0;
+      if (!f64in && n_series == 1 && total_samples % 4 == 0 && (reinterpret_cast<uintptr_t>(T) & 15u) == 0)
+        use_tma = sketch_tensor_map(&tmap, T, total_samples, d) ? 1 : 0;
       tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
+      // persistent grid: as many CTAs as are resident at once (at most one per unit)
+      auto launch = [&](auto kern, auto Tp, int smem) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSkThreads, smem) != cudaSuccess || per_sm < 1)
+          per_sm = 1;
+        const int64_t grid = std::min<int64_t>(nunits, static_cast<int64_t>(per_sm) * ctx->sm_count);
+        kern<<<static_cast<unsigned>(grid), kSkThreads, smem, st>>>(tmap, use_tma, Tp, d_cum, d_len, d_blk_prefix,
+                                                                    n_series, n_ctiles, d, dchunk, parts, wd, Rf, kp, k,
+                                                                    nc, out, pstride, ctx->d_err);
+      };
       if (f64in) {
         const double* Td = static_cast<const double*>(T);
         switch (ntm) {
-          case 1: k_sketch_bf16<double, 1><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
-          case 2: k_sketch_bf16<double, 2><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
-          case 4: k_sketch_bf16<double, 4><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
-          default: k_sketch_bf16<double, 8><<<grid_bf16, kSkThreads, 0, st>>>(Td, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          case 1: launch(k_sketch_bf16<double, 1>, Td, sk_smem_bytes(1, 8)); break;
+          case 2: launch(k_sketch_bf16<double, 2>, Td, sk_smem_bytes(2, 8)); break;
+          case 4: launch(k_sketch_bf16<double, 4>, Td, sk_smem_bytes(4, 8)); break;
+          default: launch(k_sketch_bf16<double, 8>, Td, sk_smem_bytes(8, 8)); break;
         }
       } else {
         const float* Tf = static_cast<const float*>(T);
         switch (ntm) {
-          case 1: k_sketch_bf16<float, 1><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
-          case 2: k_sketch_bf16<float, 2><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
-          case 4: k_sketch_bf16<float, 4><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
-          default: k_sketch_bf16<float, 8><<<grid_bf16, kSkThreads, 0, st>>>(Tf, d_cum, d_len, d_blk_prefix, n_series, d, dchunk, Rt, dp, k, nc, out, pstride); break;
+          case 1: launch(k_sketch_bf16<float, 1>, Tf, sk_smem_bytes(1, 4)); break;
+          case 2: launch(k_sketch_bf16<float, 2>, Tf, sk_smem_bytes(2, 4)); break;
+          case 4: launch(k_sketch_bf16<float, 4>, Tf, sk_smem_bytes(4, 4)); break;
+          default: launch(k_sketch_bf16<float, 8>, Tf, sk_smem_bytes(8, 4)); break;
         }
       }
     }

@@ -187,6 +187,70 @@ def test_sketch_build_matches_oracle(tsk, precision):
     assert np.all(np.abs(got - ref) <= tol * mag + 1e-30)
 
 
+def _exact_stat_streams(d, n, seed):
+    """(d, n) float32-exact streams whose mean and std both sides compute exactly (or to an ulp).
+
+    Each stream is a random walk on the grid 2^-10, mirrored about a dyadic centre
+    (so the mean is exactly the centre), some centres large (the float32 path's
+    |mu| term); stream 3 is constant.
+    """
+    rng = np.random.default_rng(seed)
+    half = n // 2
+    T = np.empty((d, n))
+    for j in range(d):
+        w = np.round(np.cumsum(rng.normal(size=half)) * 2.0 ** 10) / 2.0 ** 10
+        w -= np.round(w.mean() * 2.0 ** 10) / 2.0 ** 10
+        c = [0.0, 1e4, -3.5, 2048.25, -7777.0][j % 5]
+        row = np.concatenate([c + w, c - w[::-1]])
+        if n % 2:
+            row = np.append(row, c)
+        T[j] = row
+    T[3] = 5.0
+    assert np.array_equal(T.astype(np.float32).astype(np.float64), T)
+    return T
+
+
+@pytest.mark.parametrize("d", [24, 40, 100, 300])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_sketch_bf16_rounding_bit_exact(tsk, d, dtype):
+    """With R = I the bf16 sketch returns every rounded sample: each must equal the
+    oracle's nearest-even bfloat16 of its float64 z-normalised value, bit for bit
+    (ragged batch, odd lengths, large offsets, a constant stream)."""
+    series = [_exact_stat_streams(d, n, 120 + n) for n in (4099, 1000, 37)]
+    T, lens = tsk.pack_batch([torch.as_tensor(s, dtype=dtype) for s in series])
+    R = np.eye(d, dtype=np.float32)
+    S, _ = tsk.ts_sketch_build(T.cuda(), _cuda(R), lens, d, precision="bf16")
+    tsk.sync()
+    got = S.cpu().numpy().astype(np.float64)
+    off = 0
+    for s in series:
+        n = s.shape[1]
+        ref = o.bf16_round(o.global_znorm(s)[0])
+        g = got[off:off + d * n].reshape(d, n)
+        bad = np.argwhere(g != ref)
+        assert bad.size == 0, (n, bad[:5], g[tuple(bad[0])], ref[tuple(bad[0])])
+        off += d * n
+
+
+def test_sketch_bf16_many_units_per_cta_bit_exact(tsk):
+    """A batch with several times more sketch work units than resident CTAs (each
+    CTA walks many units, prefetching across their boundaries): R = I, every
+    rounded sample bit-exact against the oracle."""
+    d = 260
+    series = [_exact_stat_streams(d, 1000 + 37 * i, 300 + i) for i in range(12)]
+    T, lens = tsk.pack_batch([torch.as_tensor(s, dtype=torch.float32) for s in series])
+    S, _ = tsk.ts_sketch_build(T.cuda(), _cuda(np.eye(d, dtype=np.float32)), lens, d, precision="bf16")
+    tsk.sync()
+    got = S.cpu().numpy().astype(np.float64)
+    off = 0
+    for s in series:
+        n = s.shape[1]
+        ref = o.bf16_round(o.global_znorm(s)[0])
+        g = got[off:off + d * n].reshape(d, n)
+        assert np.array_equal(g, ref), np.argwhere(g != ref)[:5]
+        off += d * n
+
+
 @pytest.mark.parametrize("k", [65, 100, 130])
 def test_sketch_more_than_64_outputs(tsk, k):
     """k beyond one group of 64 tensor-core outputs (the sketch-quality experiment uses k = ceil(sqrt(d)))."""
