@@ -424,7 +424,8 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
 
   float acc[NTM][4];
   const int i8 = lane >> 3, r8 = lane & 7;  // ldmatrix: this lane's row of matrix i8
-  int kst = 0;  // ordinal of the next stage to process
+  int si = 0;          // slot of the next stage to process (stages rotate through the slots)
+  unsigned phase = 0;  // bit i: parity of slot i's next completion
   int ord = 0;  // unit ordinal (parity picks the partial-sum buffer)
   int uc, ug, uz;
   first_unit(uc, ug, uz);
@@ -434,12 +435,12 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
     const int NT = min(NTM, (k - I.gy * 64 + 7) >> 3);  // n8 tiles of this output group (NTM: at most)
 #pragma unroll
     for (int q = 0; q < NTM; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
-    for (int j0 = I.jb; j0 < I.je; j0 += kSkKC, ++kst) {
-      const int si = kst % kSkSlots;
+    const NormC* ncs = nc + static_cast<int64_t>(I.s) * d;
+    for (int j0 = I.jb; j0 < I.je; j0 += kSkKC) {
       const int j = j0 + lane;
       const bool jv = j < I.je;
       // constants of this lane's dimension and the stage's B fragments (both k16 steps)
-      const NormC* cp = nc + static_cast<int64_t>(I.s) * d + (jv ? j : I.jb);
+      const NormC* cp = ncs + (jv ? j : I.jb);
       const float4 cst = __ldg(reinterpret_cast<const float4*>(&cp->nmuh));
       uint4 bf[NTM];
       {
@@ -447,17 +448,35 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
 #pragma unroll
         for (int nt = 0; nt < NTM; ++nt) bf[nt] = __ldg(base + nt * 32);
       }
-      mbar_wait_bounded(&bars[si], static_cast<unsigned>((kst / kSkSlots) & 1), err);
+      mbar_wait_bounded(&bars[si], (phase >> si) & 1u, err);
+      phase ^= 1u << si;
       TIn x[16];
       {
         const unsigned char* slot = slots + si * kSlotBytes;
+        if constexpr (sizeof(TIn) == 4) {
 #pragma unroll
-        for (int c = 0; c < kChunks; ++c)
-          *reinterpret_cast<uint4*>(&x[c * (16 / kChunks)]) = *reinterpret_cast<const uint4*>(slot + sk_chunk_off<TIn>(lane, c));
+          for (int c = 0; c < 4; ++c) {
+            const float4 q = *reinterpret_cast<const float4*>(slot + sk_chunk_off<TIn>(lane, c));
+            x[4 * c] = q.x;
+            x[4 * c + 1] = q.y;
+            x[4 * c + 2] = q.z;
+            x[4 * c + 3] = q.w;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const double2 q = *reinterpret_cast<const double2*>(slot + sk_chunk_off<TIn>(lane, c));
+            x[2 * c] = q.x;
+            x[2 * c + 1] = q.y;
+          }
+        }
       }
-      __syncwarp();  // every lane has read the slot: refill it with the stage kSkSlots ahead
+      // every lane has read the slot (refill it with the stage kSkSlots ahead) and,
+      // from the previous stage, the tile's fragments (the tile may be rewritten)
+      __syncwarp();
       if (use_tma && lane == 0) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       issue(si);
+      si = si + 1 == kSkSlots ? 0 : si + 1;
       uint32_t pk[8];
       if constexpr (sizeof(TIn) == 4) {
         const float2 nmuh2 = make_float2(cst.x, cst.x), nmul2 = make_float2(cst.y, cst.y), rh2 = make_float2(cst.z, cst.z);
@@ -499,18 +518,15 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
                      : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
                      : "r"(addr));
 #pragma unroll
-        for (int nt = 0; nt < NTM; ++nt) {
-          if (nt < NT) {
-            const uint32_t b0 = ks ? bf[nt].z : bf[nt].x, b1 = ks ? bf[nt].w : bf[nt].y;
-            asm volatile(
-                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                "{%0,%1,%2,%3};\n"
-                : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-          }
+        for (int nt = 0; nt < NTM; ++nt) {  // every tile: R is zero past k, those outputs are not stored
+          const uint32_t b0 = ks ? bf[nt].z : bf[nt].x, b1 = ks ? bf[nt].w : bf[nt].y;
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+              : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
         }
       }
-      __syncwarp();  // the tile's fragments have been read before the next stage's stores
     }
     if (wd > 1) {  // add the dimension parts of each time tile in part order
       float(*rb)[NTM * 4][32] = red[ord & 1];
