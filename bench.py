@@ -41,7 +41,7 @@ FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of the k_mp_diag launches of one step, from one ncu
 # capture per workload (profiles/launches_water_bench.md); None where not taken.
-MP_DIAG_DRAM_BYTES = {"water": [13110272, 13257984, 87172096]}
+MP_DIAG_DRAM_BYTES = {"water": [13032960, 13201408, 85382912]}
 
 WORKLOADS = {
     # name: (synth workload index, top-K, description)
