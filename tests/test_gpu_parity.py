@@ -232,6 +232,20 @@ def test_sketch_bf16_rounding_bit_exact(tsk, d, dtype):
         off += d * n
 
 
+@pytest.mark.parametrize("d", [40, 300])
+def test_sketch_bf16_single_series_bit_exact(tsk, d):
+    """One float32 series whose rows are 16-byte aligned (the tensor-map staging):
+    n = 4100 leaves a last tile of 4 time points and d = 40 a last stage of 8
+    rows, both read past the series as zeros; R = I, every rounded sample
+    bit-exact against the oracle."""
+    T = _exact_stat_streams(d, 4100, 410 + d)
+    S, _ = tsk.ts_sketch_build(_cuda(T.ravel()), _cuda(np.eye(d, dtype=np.float32)), [4100], d, precision="bf16")
+    tsk.sync()
+    got = S.cpu().numpy().astype(np.float64).reshape(d, 4100)
+    ref = o.bf16_round(o.global_znorm(T)[0])
+    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
+
+
 def test_sketch_bf16_many_units_per_cta_bit_exact(tsk):
     """A batch with several times more sketch work units than resident CTAs (each
     CTA walks many units, prefetching across their boundaries): R = I, every
