@@ -132,17 +132,17 @@ __device__ __forceinline__ uint16_t tbar_bf16(double x, const NormC& c) {
 }
 // The same for two samples of one stream, packed (x0 in the low half); the
 // float32 steps run on pairs.
-// The float32 part has no branch (ok = false where float64 must decide), so a
-// caller can run several pairs side by side and fix the rare ones afterwards.
+// The float32 part has no branch: it returns the packed roundings of v - E
+// (blo) and v + E (bhi); where they differ float64 must decide.  A caller can
+// run several pairs side by side and fix the rare ones afterwards.
 __device__ __forceinline__ uint32_t tbar_bf16x2_fast(float x0, float x1, float2 nmuh2, float2 nmul2, float2 rh2, float c0,
-                                                     bool& ok) {
+                                                     uint32_t& bhi) {
   const float2 v = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(x0, x1), nmuh2), nmul2), rh2);
   const float2 e = make_float2(__fmaf_rn(fabsf(v.x), 0x1p-21f, c0), __fmaf_rn(fabsf(v.y), 0x1p-21f, c0));
   const float2 lo = __ffma2_rd(e, make_float2(-1.f, -1.f), v);
   const float2 hi = __fadd2_ru(v, e);
-  const uint32_t blo = cvt_bf16x2(lo.x, lo.y);
-  ok = blo == cvt_bf16x2(hi.x, hi.y);
-  return blo;
+  bhi = cvt_bf16x2(hi.x, hi.y);
+  return cvt_bf16x2(lo.x, lo.y);
 }
 __device__ __forceinline__ uint32_t tbar_bf16x2_f64(double x0, double x1, const NormC* __restrict__ nc) {
   const double mu = nc->mu, r = nc->r;
@@ -480,17 +480,20 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
       uint32_t pk[8];
       if constexpr (sizeof(TIn) == 4) {
         const float2 nmuh2 = make_float2(cst.x, cst.x), nmul2 = make_float2(cst.y, cst.y), rh2 = make_float2(cst.z, cst.z);
-        unsigned redo = 0;  // pairs that float32 cannot decide (about 1 in 2500)
+        uint32_t diff = 0;  // nonzero if float32 cannot decide some pair (about 1 in 2500 pairs)
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          bool ok;
-          pk[q] = tbar_bf16x2_fast(x[2 * q], x[2 * q + 1], nmuh2, nmul2, rh2, cst.w, ok);
-          redo |= ok ? 0u : (1u << q);
+          uint32_t bhi;
+          pk[q] = tbar_bf16x2_fast(x[2 * q], x[2 * q + 1], nmuh2, nmul2, rh2, cst.w, bhi);
+          diff |= pk[q] ^ bhi;
         }
-        if (redo) {
+        if (diff) {  // find the undecided pairs again and take them in float64
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (redo & (1u << q)) pk[q] = tbar_bf16x2_f64(x[2 * q], x[2 * q + 1], cp);
+          for (int q = 0; q < 8; ++q) {
+            uint32_t bhi;
+            if (tbar_bf16x2_fast(x[2 * q], x[2 * q + 1], nmuh2, nmul2, rh2, cst.w, bhi) != bhi)
+              pk[q] = tbar_bf16x2_f64(x[2 * q], x[2 * q + 1], cp);
+          }
         }
       } else {
         const double mu = cp->mu, r = cp->r;
