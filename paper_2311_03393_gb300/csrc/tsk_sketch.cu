@@ -158,19 +158,22 @@ __device__ __forceinline__ uint32_t tbar_bf16x2_f64(double x0, double x1, const 
 // word holding the lane's fragments of both k16 steps), zero past d and k, and
 // the per-stream statistics into NormC constants, once per call.
 //
-// k_sketch_bf16: a CTA of 4 warps covers 16 x (4 / wd) time points of one
-// series, one group of up to 64 outputs (blockIdx.y) and one range of
-// dimensions (blockIdx.z, only when the grid would otherwise leave SMs idle);
-// its warps split the range into wd parts (wd = 4 for d >= 256, so a CTA is one
-// m16 tile of time points and the grid has many small CTAs).  Each warp runs
-// independently over its dimensions in stages of 32: lane j loads 16
-// consecutive samples of dimension j (16-byte loads where aligned) two stages
-// ahead, converts them in pairs with one set of normalisation constants and
-// writes them with two 16-byte stores into the warp's [dimension][time] tile;
-// the A fragments come from that tile with ldmatrix.trans, no block barrier.
-// The wd partial sums of a time tile are added in a fixed order at the end,
-// and with several dimension ranges k_sketch_reduce adds those in a fixed
-// order (deterministic).
+// k_sketch_bf16: a persistent grid (the CTAs resident at once) walks work
+// units; a unit is 16 x (4 / wd) time points of one series, one group of up
+// to 64 outputs and one range of dimensions (ranges only when the grid would
+// otherwise leave SMs idle).  The 4 warps of a CTA split the range into wd
+// parts (wd = 4 for d >= 256: a unit is one m16 tile of time points) and run
+// independently over their dimensions in stages of 32.  A stage's samples (32
+// dimensions x 16 time points) arrive in one of three per-warp shared-memory
+// slots kSkSlots stages ahead: one TMA tile (cp.async.bulk.tensor, 64-byte
+// swizzle, completion on an mbarrier) for a float32 series whose rows are
+// 16-byte aligned, plain loads otherwise.  Lane j converts its 16 samples of
+// dimension j in pairs with one set of normalisation constants and writes them
+// with two 16-byte stores into the warp's [dimension][time] tile; the A
+// fragments come from that tile with ldmatrix.trans.  At the end of a unit the
+// wd partial sums of each time tile are added in a fixed order (one CTA
+// barrier per unit), and with several dimension ranges k_sketch_reduce adds
+// those in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 constexpr int kSkBlock = 64;       // time points per block of the batch layout
 constexpr int kSkThreads = 128;
