@@ -2,9 +2,10 @@
 // (Sec. III-A, Alg. 1), plus dimension addition/deletion (Sec. III-C).
 //
 // The sketch is a dense contraction over d with a tiny output width k; it is
-// bound by reading T once.  In bfloat16 mode each element of T is normalised
-// in float64, rounded to bfloat16 (nearest even) and fed to the tensor cores;
-// products are summed in float32.
+// bound by reading T once.  In bfloat16 mode each element of T becomes the
+// bfloat16 (nearest even) of its float64 normalised value, decided in float32
+// with an error interval and in float64 only where that cannot decide, and is
+// fed to the tensor cores; products are summed in float32.
 #include "tsk_internal.cuh"
 #include "tsk_ff.cuh"
 
