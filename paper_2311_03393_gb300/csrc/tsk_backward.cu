@@ -9,10 +9,11 @@
 // dS is non-zero on 2m positions per score, so it is kept compact:
 //   k_bw_windows  dS of each score (2 x m values)
 //   k_bw_dims     per (series, dim j): a_j = mean(dT_bar_j), b_j = mean(dT_bar_j T_bar_j), dR
-//   k_bw_dense    dT_j = (- a_j - T_bar_j b_j) / sigma_j everywhere
+//   k_bw_dense    dT_j = (- a_j - T_bar_j b_j) / sigma_j everywhere (one FMA per element)
 //   k_bw_scatter  dT_j += (R_jg dS_g) / sigma_j on the 2m positions of each score
 #include "tsk_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace {
@@ -125,30 +126,38 @@ __global__ void __launch_bounds__(kBwThreads) k_bw_dims(const float* __restrict_
   if (threadIdx.x == 0) { ab[2 * blockIdx.x] = sa / n; ab[2 * blockIdx.x + 1] = sb / n; }
 }
 
+// dT_j[t] = c0 + c1 (T_j[t] - mu_j) with c0 = -a_j / sigma_j, c1 = -b_j / sigma_j^2
+// (the same as (-a_j - T_bar_j[t] b_j) / sigma_j), 0 for a constant stream.  One
+// (series, stream) row at a time per CTA, its constants formed once in float64;
+// float32 series take the mean as two floats, so the centred sample is exact to
+// float32 rounding, and one FMA per element.  Coalesced passes along time.
 template <typename TIn>
-__global__ void k_bw_dense(const TIn* __restrict__ T, const double* __restrict__ stats, const double* __restrict__ ab,
-                           const int64_t* __restrict__ cum, const int32_t* __restrict__ len, int n_series, int d,
-                           int64_t total, float* __restrict__ dT) {
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  // element e of the batch: series s covers [d cum[s], d cum[s+1])
-  int lo = 0, hi = n_series - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (static_cast<int64_t>(d) * cum[mid] <= e) lo = mid; else hi = mid - 1;
+__global__ void __launch_bounds__(256) k_bw_dense(const TIn* __restrict__ T, const double* __restrict__ stats,
+                                                  const double* __restrict__ ab, const int64_t* __restrict__ cum,
+                                                  const int32_t* __restrict__ len, int n_series, int d,
+                                                  float* __restrict__ dT) {
+  const int64_t rows = static_cast<int64_t>(n_series) * d;
+  for (int64_t q = blockIdx.x; q < rows; q += gridDim.x) {
+    const int s = static_cast<int>(q / d), j = static_cast<int>(q % d);
+    const int n = len[s];
+    const int64_t base = static_cast<int64_t>(d) * cum[s] + static_cast<int64_t>(j) * n;
+    const double sg = stats[2 * q + 1];
+    if (!(sg > 0.0)) {
+      for (int t = threadIdx.x; t < n; t += blockDim.x) dT[base + t] = 0.f;
+      continue;
+    }
+    const double mu = stats[2 * q], r = 1.0 / sg;
+    const double c0 = -ab[2 * q] * r, c1 = -ab[2 * q + 1] * r * r;
+    if constexpr (sizeof(TIn) == 4) {
+      const float muh = static_cast<float>(mu), mul = static_cast<float>(mu - static_cast<double>(muh));
+      const float f0 = static_cast<float>(c0), f1 = static_cast<float>(c1);
+      for (int t = threadIdx.x; t < n; t += blockDim.x)
+        dT[base + t] = __fmaf_rn(f1, __fsub_rn(__fsub_rn(T[base + t], muh), mul), f0);
+    } else {
+      for (int t = threadIdx.x; t < n; t += blockDim.x)
+        dT[base + t] = static_cast<float>(c0 + c1 * (static_cast<double>(T[base + t]) - mu));
+    }
   }
-  const int s = lo;
-  const int n = len[s];
-  const int64_t rel = e - static_cast<int64_t>(d) * cum[s];
-  const int j = static_cast<int>(rel / n);
-  const int64_t q = static_cast<int64_t>(s) * d + j;
-  const double sg = stats[2 * q + 1];
-  float out = 0.f;
-  if (sg > 0) {
-    const double tb = (static_cast<double>(T[e]) - stats[2 * q]) / sg;
-    out = static_cast<float>((-ab[2 * q] - tb * ab[2 * q + 1]) / sg);
-  }
-  dT[e] = out;
 }
 
 __global__ void k_bw_scatter(const float* __restrict__ dSc, const int32_t* __restrict__ idx, const int32_t* __restrict__ grp,
@@ -191,18 +200,17 @@ tsk_status tsk_launch_backward(tsk_ctx* ctx, const float* dscore, const int32_t*
   k_bw_windows<<<static_cast<unsigned>(nsel), kBwThreads, 0, st>>>(dscore, idx, grp, nn, K, S, d_cum, d_len, k, m, dSc);
   TSK_LAUNCH_CHECK(ctx, "k_bw_windows");
   const unsigned nd = static_cast<unsigned>(static_cast<int64_t>(n_series) * d);
-  const int64_t tot = static_cast<int64_t>(d) * total_samples;
-  const unsigned dblocks = static_cast<unsigned>((tot + 255) / 256);
+  const unsigned dblocks = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(nd), int64_t(ctx->sm_count) * 8)));
   const int64_t sc = nsel * 2 * m;
   const unsigned sblocks = static_cast<unsigned>((sc + 255) / 256);
   if (t_dtype == TSK_F64) {
     k_bw_dims<double><<<nd, kBwThreads, 0, st>>>(dSc, idx, grp, nn, K, static_cast<const double*>(T), stats, R, d_cum, d_len, d, k, m, ab, dR);
     TSK_LAUNCH_CHECK(ctx, "k_bw_dims");
-    k_bw_dense<double><<<dblocks, 256, 0, st>>>(static_cast<const double*>(T), stats, ab, d_cum, d_len, n_series, d, tot, dT);
+    k_bw_dense<double><<<dblocks, 256, 0, st>>>(static_cast<const double*>(T), stats, ab, d_cum, d_len, n_series, d, dT);
   } else {
     k_bw_dims<float><<<nd, kBwThreads, 0, st>>>(dSc, idx, grp, nn, K, static_cast<const float*>(T), stats, R, d_cum, d_len, d, k, m, ab, dR);
     TSK_LAUNCH_CHECK(ctx, "k_bw_dims");
-    k_bw_dense<float><<<dblocks, 256, 0, st>>>(static_cast<const float*>(T), stats, ab, d_cum, d_len, n_series, d, tot, dT);
+    k_bw_dense<float><<<dblocks, 256, 0, st>>>(static_cast<const float*>(T), stats, ab, d_cum, d_len, n_series, d, dT);
   }
   TSK_LAUNCH_CHECK(ctx, "k_bw_dense");
   if (sblocks > 0) {

@@ -410,9 +410,13 @@ def test_batched_ragged_series_sketched(tsk):
 
 # --- adjoint --------------------------------------------------------------------
 
-def test_backward_matches_oracle_adjoint(tsk):
+@pytest.mark.parametrize("offset", [0.0, 1e4], ids=["centred", "offset1e4"])
+def test_backward_matches_oracle_adjoint(tsk, offset):
+    """Adjoint of the summed top-3 scores; with a large offset the dense term
+    (-a_j - T_bar_j b_j) / sigma_j must still come from well-centred samples."""
     d, n, m, k, K = 12, 3000, 60, 4, 3
     T, _ = synth.random_walks(d, n, m, 3, seed=117)
+    T = (T + offset).astype(T.dtype)
     R = synth.gaussian_R(d, k, 118)
     Tt = _cuda(T.ravel()).requires_grad_(True)
     Rt = _cuda(R).requires_grad_(True)
