@@ -19,6 +19,7 @@ generator).
 
   python -m paper_2311_03393_gb300.experiments --d 250 500 1000 --trials 20
   python -m paper_2311_03393_gb300.experiments sketch --d 1024 --n 100000 --k 16
+  python -m paper_2311_03393_gb300.experiments dims --d 1024 --n 20000 --m 144 --k 16 --K 10
 """
 from __future__ import annotations
 
@@ -161,6 +162,40 @@ def sketch_throughput(d: int, n: int, k: int, reps: int = 5, seed: int = synth.S
             "gb_per_s": (4.0 * d * n + 4.0 * k * n) / (per / 1e3) / 1e9}
 
 
+def dims_throughput(d: int, n: int, m: int, k: int, K: int, reps: int = 5, seed: int = synth.SEED_BASE,
+                    device=None) -> dict:
+    """Time Alg. 3 (the dimension scan) for the K top sketch discords of one random-walk series.
+
+    The series is (d, n) random walks, R a seeded Gaussian d x k (every
+    dimension in every group, so each discord scans all d streams), the
+    discords those of the bf16 sketch's profiles.  Reports the scan kernel's
+    device time per launch (library events) and its FMA rate: each (discord,
+    stream) scores every window with an m-sample dot product.
+    """
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    excl = api.default_excl(m)
+    T = random_walks_device(d, n, seed, device)
+    R = torch.from_numpy(synth.gaussian_R(d, k, seed + 1)).to(device)
+    S, _ = api.ts_sketch_build(T, R, [n], d, precision="bf16")
+    P, I = api.mp_selfjoin(S, [n] * k, m, excl)
+    idx, grp, _, _ = api.discord_topk(P, I, [n], k, m, K)
+    for _ in range(2):
+        api.dimension_detection(T, R, [n], d, m, idx, grp, excl)
+    api.sync()
+    api.profile_enable(True)
+    api.profile_read("dims")
+    for _ in range(reps):
+        api.dimension_detection(T, R, [n], d, m, idx, grp, excl)
+    api.sync()
+    ms, launches = api.profile_read("dims")
+    api.profile_enable(False)
+    per = ms / max(launches, 1)
+    found = int((idx[0] >= 0).sum().item())
+    fmas = float(found) * d * (n - m + 1) * m
+    return {"d": d, "n": n, "m": m, "k": k, "K": K, "discords": found, "ms_per_launch": per,
+            "tfma_per_s": fmas / (per / 1e3) / 1e12}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd")
@@ -177,6 +212,13 @@ def main(argv=None):
     t.add_argument("--k", type=int, default=16)
     t.add_argument("--reps", type=int, default=5)
     t.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    a = sub.add_parser("dims", help="time of the Alg. 3 dimension scan on one series")
+    a.add_argument("--d", type=int, default=1024)
+    a.add_argument("--n", type=int, default=20000)
+    a.add_argument("--m", type=int, default=144)
+    a.add_argument("--k", type=int, default=16)
+    a.add_argument("--K", type=int, default=10)
+    a.add_argument("--reps", type=int, default=5)
     argv = list(argv) if argv is not None else None
     import sys
     raw = sys.argv[1:] if argv is None else argv
@@ -185,6 +227,9 @@ def main(argv=None):
     args = ap.parse_args(raw)
     if args.cmd == "sketch":
         print(json.dumps(sketch_throughput(args.d, args.n, args.k, args.reps, precision=args.precision)), flush=True)
+        return
+    if args.cmd == "dims":
+        print(json.dumps(dims_throughput(args.d, args.n, args.m, args.k, args.K, args.reps)), flush=True)
         return
     for d in args.d:
         out = sketch_quality(d, args.n, args.m, args.trials, seed=args.seed, sketch_precision=args.sketch_precision)
