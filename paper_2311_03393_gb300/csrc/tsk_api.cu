@@ -848,6 +848,8 @@ extern "C" TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, con
   const size_t need = tsk_carver::bytes_for(static_cast<size_t>(nsel) * 2 * m, 4) +
                       tsk_carver::bytes_for(static_cast<size_t>(n_series) * d * 2, 8);
   if ((st = tsk_ws_require(ctx, need))) return st;
+  int32_t max_len = 0;
+  for (int32_t q = 0; q < n_series; ++q) max_len = std::max(max_len, series_len_host[q]);
   return tsk_launch_backward(ctx, dscore, idx, grp, nn, K, T, t_dtype, stats, R, S, n_series, L.cum, L.len,
-                             L.total_samples, d, k, m, dT, dR, static_cast<char*>(ctx->ws));
+                             L.total_samples, max_len, d, k, m, dT, dR, static_cast<char*>(ctx->ws));
 }

@@ -127,23 +127,30 @@ __global__ void __launch_bounds__(kBwThreads) k_bw_dims(const float* __restrict_
 }
 
 // dT_j[t] = c0 + c1 (T_j[t] - mu_j) with c0 = -a_j / sigma_j, c1 = -b_j / sigma_j^2
-// (the same as (-a_j - T_bar_j[t] b_j) / sigma_j), 0 for a constant stream.  One
-// (series, stream) row at a time per CTA, its constants formed once in float64;
-// float32 series take the mean as two floats, so the centred sample is exact to
-// float32 rounding, and one FMA per element.  Coalesced passes along time.
+// (the same as (-a_j - T_bar_j[t] b_j) / sigma_j), 0 for a constant stream.  A
+// CTA takes a chunk of kBwChunk samples of one (series, stream) row at a time,
+// the row's constants formed in float64; float32 series take the mean as two
+// floats, so the centred sample is exact to float32 rounding, and one FMA per
+// element.  Coalesced passes along time.
+constexpr int kBwChunk = 4096;  // samples of a row per work item of k_bw_dense
+
 template <typename TIn>
 __global__ void __launch_bounds__(256) k_bw_dense(const TIn* __restrict__ T, const double* __restrict__ stats,
                                                   const double* __restrict__ ab, const int64_t* __restrict__ cum,
                                                   const int32_t* __restrict__ len, int n_series, int d,
-                                                  float* __restrict__ dT) {
-  const int64_t rows = static_cast<int64_t>(n_series) * d;
-  for (int64_t q = blockIdx.x; q < rows; q += gridDim.x) {
+                                                  int chunks_per_row, float* __restrict__ dT) {
+  const int64_t items = static_cast<int64_t>(n_series) * d * chunks_per_row;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t q = it / chunks_per_row;
     const int s = static_cast<int>(q / d), j = static_cast<int>(q % d);
     const int n = len[s];
+    const int t0 = static_cast<int>(it % chunks_per_row) * kBwChunk;
+    if (t0 >= n) continue;
+    const int t1 = min(n, t0 + kBwChunk);
     const int64_t base = static_cast<int64_t>(d) * cum[s] + static_cast<int64_t>(j) * n;
     const double sg = stats[2 * q + 1];
     if (!(sg > 0.0)) {
-      for (int t = threadIdx.x; t < n; t += blockDim.x) dT[base + t] = 0.f;
+      for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) dT[base + t] = 0.f;
       continue;
     }
     const double mu = stats[2 * q], r = 1.0 / sg;
@@ -151,10 +158,10 @@ __global__ void __launch_bounds__(256) k_bw_dense(const TIn* __restrict__ T, con
     if constexpr (sizeof(TIn) == 4) {
       const float muh = static_cast<float>(mu), mul = static_cast<float>(mu - static_cast<double>(muh));
       const float f0 = static_cast<float>(c0), f1 = static_cast<float>(c1);
-      for (int t = threadIdx.x; t < n; t += blockDim.x)
+      for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
         dT[base + t] = __fmaf_rn(f1, __fsub_rn(__fsub_rn(T[base + t], muh), mul), f0);
     } else {
-      for (int t = threadIdx.x; t < n; t += blockDim.x)
+      for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
         dT[base + t] = static_cast<float>(c0 + c1 * (static_cast<double>(T[base + t]) - mu));
     }
   }
@@ -189,8 +196,8 @@ __global__ void k_bw_scatter(const float* __restrict__ dSc, const int32_t* __res
 tsk_status tsk_launch_backward(tsk_ctx* ctx, const float* dscore, const int32_t* idx, const int32_t* grp,
                                const int32_t* nn, int32_t K, const void* T, int t_dtype, const double* stats,
                                const float* R, const float* S, int32_t n_series, const int64_t* d_cum,
-                               const int32_t* d_len, int64_t total_samples, int32_t d, int32_t k, int32_t m,
-                               float* dT, float* dR, char* ws) {
+                               const int32_t* d_len, int64_t total_samples, int32_t max_len, int32_t d, int32_t k,
+                               int32_t m, float* dT, float* dR, char* ws) {
   tsk_carver cv(ws);
   const int64_t nsel = static_cast<int64_t>(n_series) * K;
   float* dSc = cv.take<float>(nsel * 2 * m);
@@ -200,17 +207,19 @@ tsk_status tsk_launch_backward(tsk_ctx* ctx, const float* dscore, const int32_t*
   k_bw_windows<<<static_cast<unsigned>(nsel), kBwThreads, 0, st>>>(dscore, idx, grp, nn, K, S, d_cum, d_len, k, m, dSc);
   TSK_LAUNCH_CHECK(ctx, "k_bw_windows");
   const unsigned nd = static_cast<unsigned>(static_cast<int64_t>(n_series) * d);
-  const unsigned dblocks = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(nd), int64_t(ctx->sm_count) * 8)));
+  const int chunks_per_row = std::max(1, (max_len + kBwChunk - 1) / kBwChunk);
+  const int64_t items = static_cast<int64_t>(nd) * chunks_per_row;
+  const unsigned dblocks = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(items, int64_t(ctx->sm_count) * 8)));
   const int64_t sc = nsel * 2 * m;
   const unsigned sblocks = static_cast<unsigned>((sc + 255) / 256);
   if (t_dtype == TSK_F64) {
     k_bw_dims<double><<<nd, kBwThreads, 0, st>>>(dSc, idx, grp, nn, K, static_cast<const double*>(T), stats, R, d_cum, d_len, d, k, m, ab, dR);
     TSK_LAUNCH_CHECK(ctx, "k_bw_dims");
-    k_bw_dense<double><<<dblocks, 256, 0, st>>>(static_cast<const double*>(T), stats, ab, d_cum, d_len, n_series, d, dT);
+    k_bw_dense<double><<<dblocks, 256, 0, st>>>(static_cast<const double*>(T), stats, ab, d_cum, d_len, n_series, d, chunks_per_row, dT);
   } else {
     k_bw_dims<float><<<nd, kBwThreads, 0, st>>>(dSc, idx, grp, nn, K, static_cast<const float*>(T), stats, R, d_cum, d_len, d, k, m, ab, dR);
     TSK_LAUNCH_CHECK(ctx, "k_bw_dims");
-    k_bw_dense<float><<<dblocks, 256, 0, st>>>(static_cast<const float*>(T), stats, ab, d_cum, d_len, n_series, d, dT);
+    k_bw_dense<float><<<dblocks, 256, 0, st>>>(static_cast<const float*>(T), stats, ab, d_cum, d_len, n_series, d, chunks_per_row, dT);
   }
   TSK_LAUNCH_CHECK(ctx, "k_bw_dense");
   if (sblocks > 0) {
