@@ -851,5 +851,5 @@ extern "C" TSK_API tsk_status mp_backward(tsk_ctx* ctx, const float* dscore, con
   int32_t max_len = 0;
   for (int32_t q = 0; q < n_series; ++q) max_len = std::max(max_len, series_len_host[q]);
   return tsk_launch_backward(ctx, dscore, idx, grp, nn, K, T, t_dtype, stats, R, S, n_series, L.cum, L.len,
-                             L.total_samples, max_len, d, k, m, dT, dR, static_cast<char*>(ctx->ws));
+                             max_len, d, k, m, dT, dR, static_cast<char*>(ctx->ws));
 }

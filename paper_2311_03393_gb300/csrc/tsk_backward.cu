@@ -196,7 +196,7 @@ __global__ void k_bw_scatter(const float* __restrict__ dSc, const int32_t* __res
 tsk_status tsk_launch_backward(tsk_ctx* ctx, const float* dscore, const int32_t* idx, const int32_t* grp,
                                const int32_t* nn, int32_t K, const void* T, int t_dtype, const double* stats,
                                const float* R, const float* S, int32_t n_series, const int64_t* d_cum,
-                               const int32_t* d_len, int64_t total_samples, int32_t max_len, int32_t d, int32_t k,
+                               const int32_t* d_len, int32_t max_len, int32_t d, int32_t k,
                                int32_t m, float* dT, float* dR, char* ws) {
   tsk_carver cv(ws);
   const int64_t nsel = static_cast<int64_t>(n_series) * K;

@@ -221,5 +221,5 @@ tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, const void* T_train, int
 tsk_status tsk_launch_backward(tsk_ctx* ctx, const float* dscore, const int32_t* idx, const int32_t* grp,
                                const int32_t* nn, int32_t K, const void* T, int t_dtype, const double* stats,
                                const float* R, const float* S, int32_t n_series, const int64_t* d_cum,
-                               const int32_t* d_len, int64_t total_samples, int32_t max_len, int32_t d, int32_t k,
+                               const int32_t* d_len, int32_t max_len, int32_t d, int32_t k,
                                int32_t m, float* dT, float* dR, char* ws);
