@@ -458,6 +458,44 @@ def test_abjoin_against_brute_force_pairs():
         assert abs(P[i] - dists[jb]) <= 1e-9 and I[i] == jb
 
 
+def test_abjoin_rows_against_brute_force_pairs():
+    """abjoin_rows (the sampled-row form the full-size GPU tests use) against scipy z-scores, every row."""
+    rng = np.random.default_rng(43)
+    a = np.cumsum(rng.normal(size=48))
+    b = np.cumsum(rng.normal(size=31))
+    a[10:18] = -1.0                                  # constant test windows
+    m = 7
+    Za, Zb = _zscore_windows_scipy(a, m), _zscore_windows_scipy(b, m)
+    rows = list(range(len(Za)))
+    P, I = o.abjoin_rows(a, b, m, rows)
+    for r, i in enumerate(rows):
+        dists = [float(np.linalg.norm(Za[i] - Zb[j])) for j in range(len(Zb))]
+        jb = min(range(len(dists)), key=lambda j: (dists[j], j))
+        assert abs(P[r] - dists[jb]) <= 1e-9 and I[r] == jb
+
+
+def test_exact_discords_against_brute_force_profiles():
+    """exact_discords (Def. 5 over the raw dimensions, then Alg. 2's ranked list) against
+    per-dimension brute-force profiles from scipy z-scores, aggregated and ranked by hand."""
+    rng = np.random.default_rng(44)
+    d, n, m, K = 3, 70, 8, 3
+    T = np.cumsum(rng.normal(size=(d, n)), axis=1)
+    excl = 2
+    l = n - m + 1
+    P = np.array([[_brute_row(T[j], m, excl, i)[0] for i in range(l)] for j in range(d)])
+    I = np.array([[_brute_row(T[j], m, excl, i)[1] for i in range(l)] for j in range(d)])
+    A = P.max(axis=0)
+    G = np.array([min(j for j in range(d) if P[j, i] == A[i]) for i in range(l)])
+    want, Am = [], A.copy()
+    for _ in range(K):
+        i = int(np.argmax(Am))
+        want.append((i, int(G[i]), float(A[i]), int(I[G[i], i])))
+        Am[max(0, i - m + 1):i + m] = -np.inf
+    got = o.exact_discords(T, m, excl, K, m)
+    assert [(g[0], g[1], g[3]) for g in got] == [(w[0], w[1], w[3]) for w in want]
+    assert np.allclose([g[2] for g in got], [w[2] for w in want], rtol=0, atol=1e-9)
+
+
 def test_abjoin_of_a_series_with_itself_is_zero_and_the_closest_pair_is_shared():
     rng = np.random.default_rng(42)
     x = np.cumsum(rng.normal(size=300))
