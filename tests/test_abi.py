@@ -61,3 +61,45 @@ def test_dimension_detection_rejects_a_null_context(libpath):
     lib = _native.lib()
     assert lib.dimension_detection(None, None, 0, 0, None, 0, None, 0, 0, 0, 0, None, None, None, None, None,
                                    None, None, None, None, None) == 1
+
+
+
+def _null_args(argtypes):
+    """NULL for every pointer argument, 0 for every number."""
+    import ctypes as C
+    return [None if isinstance(a, type) and issubclass(a, (C._Pointer, C.c_void_p, C.c_char_p)) else 0
+            for a in argtypes]
+
+
+@pytest.mark.parametrize("name", sorted(n for n, (_, args) in _native.SIGNATURES.items()
+                                        if args and args[0] is _native._P
+                                        and n not in ("tsk_create", "tsk_destroy", "mp_selfjoin_static")))
+def test_every_context_call_rejects_a_null_context(libpath, name):
+    """Every entry point that takes a context returns TSK_ERR_INVALID_ARG for NULL (nothing
+    launched); tsk_launch_count reports -1 and tsk_last_error says what was wrong."""
+    lib = _native.lib()
+    got = getattr(lib, name)(*_null_args(_native.SIGNATURES[name][1]))
+    if name == "tsk_launch_count":
+        assert got == -1
+    elif name == "tsk_last_error":
+        assert got == b"null context"
+    else:
+        assert _native.STATUS_NAMES.get(got) == "TSK_ERR_INVALID_ARG", (name, got)
+
+
+@pytest.mark.parametrize("args", [
+    dict(X=False, n=200, m=20, excl=5),              # no input
+    dict(X=True, n=200, m=1, excl=5),                # m < 2
+    dict(X=True, n=200, m=5000, excl=5),             # m > 4096
+    dict(X=True, n=19, m=20, excl=5),                # n < m
+    dict(X=True, n=200, m=20, excl=0),               # no exclusion zone
+    dict(X=True, n=70000, m=20, excl=5),             # more windows than the static scratch holds
+], ids=["null", "m1", "m_big", "n_small", "excl0", "too_long"])
+def test_allocation_free_profile_rejects_bad_arguments_before_any_cuda_call(libpath, args):
+    """mp_selfjoin_static checks its arguments before touching CUDA, so this runs without a GPU;
+    the dummy device pointers are never dereferenced."""
+    import ctypes as C
+    lib = _native.lib()
+    X = C.c_void_p(16) if args["X"] else None
+    st = lib.mp_selfjoin_static(X, args["n"], args["m"], args["excl"], C.c_void_p(16), C.c_void_p(16), None)
+    assert _native.STATUS_NAMES.get(st) == "TSK_ERR_INVALID_ARG"
