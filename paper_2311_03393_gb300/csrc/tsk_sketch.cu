@@ -809,8 +809,10 @@ tsk_status tsk_launch_sketch(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n
         use_tma = sketch_tensor_map(&tmap, T, total_samples, d) ? 1 : 0;
       tsk_prof_scope ps(ctx, TSK_PROF_SKETCH);
       // persistent grid: as many CTAs as are resident at once (at most one per unit)
+      cudaError_t attr_err = cudaSuccess;
       auto launch = [&](auto kern, auto Tp, int smem) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (attr_err != cudaSuccess) return;
         int per_sm = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSkThreads, smem) != cudaSuccess || per_sm < 1)
           per_sm = 1;
@@ -836,6 +838,7 @@ tsk_status tsk_launch_sketch(tsk_ctx* ctx, const void* T, int t_dtype, int32_t n
           default: launch(k_sketch_bf16<float, 8>, Tf, sk_smem_bytes(8, 4)); break;
         }
       }
+      if (attr_err != cudaSuccess) return tsk_cuda_fail(ctx, attr_err, "k_sketch_bf16 shared-memory size");
     }
     TSK_LAUNCH_CHECK(ctx, "k_sketch_bf16");
     if (parts > 1) {
