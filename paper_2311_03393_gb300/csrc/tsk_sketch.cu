@@ -257,7 +257,7 @@ __host__ __device__ constexpr int sk_slot_bytes(int elem) { return kSkKC * 16 * 
 // dynamic shared memory: [slots: warps x kSkSlots stages][tiles: warps x 1.5 KB][partial sums][mbarriers]
 __host__ __device__ constexpr int sk_smem_bytes(int ntm, int elem) {
   return kSkWarps * kSkSlots * sk_slot_bytes(elem) + kSkWarps * kSkTileBytes + 2 * kSkWarps * ntm * 4 * 32 * 4 +
-         kSkWarps * kSkSlots * 8;
+         kSkWarps * kSkSlots * 8 + 16;
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
@@ -279,17 +279,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the barrier's phase `parity` to complete, at most ~1 s (then flag a
-// timeout in the error word and return: the data are not valid).
-__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
-  if (mbar_try_wait(bar, parity)) return;
+// Wait for the barrier's phase `parity` to complete, at most ~1 s.  Returns
+// false after flagging a timeout in the error word (the data are not valid).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > (1LL << 31)) {
       atomicOr(err, TSK_DEVERR_TIMEOUT);
-      return;
+      return false;
     }
   }
+  return true;
 }
 // 2-D tile (x: time, y: dimension) of the tensor map into shared memory, completing on bar
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -327,6 +328,11 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
   uint64_t* bars = reinterpret_cast<uint64_t*>(sk_smem + kSkWarps * kSkSlots * kSlotBytes + kSkWarps * kSkTileBytes +
                                                2 * kSkWarps * NTM * 4 * 32 * 4) +
                    warp * kSkSlots;
+  // abort flags, one per unit parity: set by a warp whose copy never landed,
+  // read by every warp after that unit's block barrier
+  volatile int* abortf = reinterpret_cast<volatile int*>(sk_smem + kSkWarps * kSkSlots * kSlotBytes +
+                                                         kSkWarps * kSkTileBytes + 2 * kSkWarps * NTM * 4 * 32 * 4 +
+                                                         kSkWarps * kSkSlots * 8);
 
   const int tsub = warp / wd, dpart = warp % wd;
   const int gid = lane >> 2, tig = lane & 3;
@@ -340,7 +346,8 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
     for (int i = 0; i < kSkSlots; ++i) mbar_init(&bars[i], 1);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
-  __syncwarp();
+  if (tid == 0) abortf[0] = abortf[1] = 0;
+  __syncthreads();
 
   // unit u = c + C (gy + kgroups z): CTA tile c (wd per 64-point block, each
   // 16 x (4 / wd) time points), output group gy, dimension range z.  A CTA
@@ -396,8 +403,10 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
   // fetch the cursor's stage into slot i: one TMA tile (rows past d and time
   // points past n arrive as zeros), or, without a tensor map, each lane's row
   // by plain loads; then advance the cursor
+  unsigned pending = 0;  // bit i: slot i has a stage issued and not yet waited for
   auto issue = [&](int i) {
     if (pz >= parts) return;
+    pending |= 1u << i;
     unsigned char* slot = slots + i * kSlotBytes;
     if (use_tma) {
       if (lane == 0) {
@@ -431,6 +440,7 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
   int si = 0;          // slot of the next stage to process (stages rotate through the slots)
   unsigned phase = 0;  // bit i: parity of slot i's next completion
   int ord = 0;  // unit ordinal (parity picks the partial-sum buffer)
+  bool dead = false;  // warp-uniform: a wait gave up; no more copies are issued
   int uc, ug, uz;
   first_unit(uc, ug, uz);
   for (; uz < parts; next_unit(uc, ug, uz), ++ord) {
@@ -452,7 +462,11 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
 #pragma unroll
         for (int nt = 0; nt < NTM; ++nt) bf[nt] = __ldg(base + nt * 32);
       }
-      mbar_wait_bounded(&bars[si], (phase >> si) & 1u, err);
+      if (!__all_sync(TSK_FULL_MASK, mbar_wait_bounded(&bars[si], (phase >> si) & 1u, err))) {
+        dead = true;  // leave within one wait limit: the unit's result is not valid
+        break;
+      }
+      pending &= ~(1u << si);
       phase ^= 1u << si;
       TIn x[16];
       {
@@ -541,7 +555,9 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
       for (int nt = 0; nt < NTM; ++nt)
 #pragma unroll
         for (int c = 0; c < 4; ++c) rb[warp][nt * 4 + c][lane] = acc[nt][c];
+      if (dead && lane == 0) abortf[ord & 1] = 1;
       __syncthreads();  // also: every warp has finished reading the buffer of two units ago
+      if (abortf[ord & 1]) break;  // every warp of the block leaves at the same unit
       if (dpart != 0) continue;
 #pragma unroll
       for (int nt = 0; nt < NTM; ++nt)
@@ -552,6 +568,7 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
           acc[nt][c] = v;
         }
     }
+    if (dead) break;  // one warp per time tile (no block barrier): leave alone
     if (I.nv <= 0) continue;
 #pragma unroll
     for (int nt = 0; nt < NTM; ++nt) {
@@ -569,6 +586,10 @@ __global__ void __launch_bounds__(kSkThreads, sizeof(TIn) == 8 ? 2 : (NTM <= 2 ?
       }
     }
   }
+  // after an abort, copies may still be in flight into this block's slots: wait
+  // for each (again at most ~1 s) before the block's shared memory is released
+  for (int i = 0; i < kSkSlots; ++i)
+    if (pending & (1u << i)) mbar_wait_bounded(&bars[i], (phase >> i) & 1u, err);
 }
 
 // S = sum over the dimension ranges of the partial sketches, in range order
