@@ -210,6 +210,33 @@ TSK_API tsk_status mp_selfjoin(tsk_ctx* ctx, const void* X, int32_t x_dtype, int
                                int32_t excl, int32_t precision, void* P, int32_t* I);
 
 /*
+ * mp_selfjoin_update - the self-join profile of float32 streams after point
+ * updates: Sec. III-C's point update moves a sketch stream at single times
+ * (ts_sketch_point_update), and the profile follows incrementally, the
+ * streaming use Sec. III-B names.  A changed sample t moves windows
+ * t-m+1 .. t (set A).  Windows of A get their whole row anew; a window whose
+ * old nearest neighbour was in A is re-scanned whole; every other window
+ * keeps its old value unless a window of A is now nearer.  The result is the
+ * profile mp_selfjoin would compute for the updated streams (Def. 6), at a
+ * cost of about (2|A| + 512) l + |R| l m operations per stream instead of l^2.
+ *   X               : device float32 streams, already updated, stream layout.
+ *   stream_len_host : int32 [n_streams] HOST.
+ *   m, excl         : as given to the mp_selfjoin call that produced P, I.
+ *   P, I            : device float32 / int32, stream layout: on entry the
+ *                     profile of the streams before the updates (as
+ *                     mp_selfjoin, TSK_MP_FP32, wrote it), on return the
+ *                     profile after them.  Streams with no point are untouched.
+ *   pt_stream_host, pt_time_host : n_pts HOST (stream, time) pairs, the
+ *                     samples that changed (repeats allowed); read before the
+ *                     call returns.
+ * Errors: TSK_ERR_INVALID_ARG for NULL arrays, bad m / excl, or a point out of
+ * range (nothing issued).
+ */
+TSK_API tsk_status mp_selfjoin_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int32_t* stream_len_host,
+                                      int32_t m, int32_t excl, float* P, int32_t* I, int32_t n_pts,
+                                      const int32_t* pt_stream_host, const int32_t* pt_time_host);
+
+/*
  * mp_abjoin - AB-join matrix profile (Def. 6 with T_test != T_train), the
  * form Alg. 2 runs on: for every window i of test stream A_q,
  *   P_a[i] = min over EVERY window j of training stream B_q of dist(A_q[i:i+m], B_q[j:j+m]),
@@ -337,9 +364,10 @@ TSK_API tsk_status dimension_detection(tsk_ctx* ctx, const void* T, int32_t t_dt
  * memory is owned by another framework's pool, or code called back from
  * inside an allocator, where allocating again would deadlock or fail.
  *
- * All scratch (window statistics, the per-window maxima, the work list and
- * counters) lives in one 3 MiB array in the library's global device memory;
- * every GPU that loads the library holds that array until the process exits.
+ * All scratch (window statistics, the per-window maxima and near-tie
+ * candidates, the work list and counters) lives in one 6 MiB array in the
+ * library's global device memory; every GPU that loads the library holds that
+ * array until the process exits.
  *   X      : device float32 [n] input stream (caller-owned).
  *   P, I   : device float32 / int32 [n] outputs, as mp_selfjoin (entries
  *            i >= l = n - m + 1 are NaN / -1).

@@ -16,6 +16,7 @@ from .api import (  # noqa: F401
     mp_abjoin,
     mp_backward,
     mp_selfjoin,
+    mp_selfjoin_update,
     pack_batch,
     profile_enable,
     profile_read,

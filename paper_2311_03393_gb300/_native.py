@@ -48,6 +48,7 @@ SIGNATURES = {
     "dimension_detection": (_I32, [_P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _P,
                                    _P, _P, _P, _P, _P]),
     "mp_selfjoin_static": (_I32, [_P, _I32, _I32, _I32, _P, _P, _P]),
+    "mp_selfjoin_update": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _P, _I32, _P, _P]),
 }
 
 _lib = None

@@ -175,6 +175,30 @@ def mp_selfjoin(X: torch.Tensor, stream_len: Sequence[int], m: int, excl: int | 
     return P, I
 
 
+def mp_selfjoin_update(X: torch.Tensor, stream_len: Sequence[int], m: int, P: torch.Tensor, I: torch.Tensor,
+                       points, excl: int | None = None):
+    """Update the self-join profile (P, I) of float32 streams X in place after point changes.
+
+    X already holds the changed samples; P, I are mp_selfjoin's (fp32) output
+    for the streams before the change.  points: (stream, time) pairs of the
+    samples that changed.  Only the windows covering them, and the windows whose
+    nearest neighbour was one of those, are re-profiled (Sec. III-C point
+    updates followed incrementally).  Returns (P, I).
+    """
+    _need_cuda(X, P, I)
+    if X.dtype != torch.float32 or P.dtype != torch.float32:
+        raise TypeError("mp_selfjoin_update needs float32 streams and a float32 profile")
+    excl = default_excl(m) if excl is None else int(excl)
+    pts = np.asarray(list(points), dtype=np.int64).reshape(-1, 2)
+    qs, qp = _i32_array(pts[:, 0])
+    ts, tp = _i32_array(pts[:, 1])
+    lens, lp = _i32_array(stream_len)
+    h = _ctx(X.device)
+    N.check(N.lib().mp_selfjoin_update(h, _ptr(X), len(stream_len), lp, int(m), excl, _ptr(P), _ptr(I),
+                                       len(pts), qp, tp), h, "mp_selfjoin_update")
+    return P, I
+
+
 def mp_abjoin(A: torch.Tensor, B: torch.Tensor, len_a: Sequence[int], len_b: Sequence[int], m: int,
               train_profile: bool = False, precision: str = "fp32"):
     """AB-join profiles (Def. 6): each test window of A_q against every window of B_q.

@@ -731,6 +731,54 @@ extern "C" TSK_API tsk_status mp_selfjoin(tsk_ctx* ctx, const void* X, int32_t x
   return tsk_run_mp(ctx, X, x_dtype, n_streams, plan, m, excl, precision, P, I, static_cast<char*>(ctx->ws));
 }
 
+extern "C" TSK_API tsk_status mp_selfjoin_update(tsk_ctx* ctx, const float* X, int32_t n_streams,
+                                                 const int32_t* stream_len_host, int32_t m, int32_t excl, float* P,
+                                                 int32_t* I, int32_t n_pts, const int32_t* pt_stream_host,
+                                                 const int32_t* pt_time_host) {
+  tsk_status st = enter(ctx);
+  if (st) return st;
+  if (!X || !P || !I) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_selfjoin_update: X, P and I must be non-NULL");
+  if (n_streams < 1) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_selfjoin_update: n_streams must be >= 1");
+  if (m < 2 || m > 4096) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_selfjoin_update: need 2 <= m <= 4096 (got %d)", m);
+  if (excl < 1) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_selfjoin_update: excl must be >= 1");
+  if (n_pts < 0) return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_selfjoin_update: n_pts must be >= 0");
+  if ((st = check_lens(ctx, n_streams, stream_len_host, m, "mp_selfjoin_update"))) return st;
+  if (n_pts == 0) return TSK_OK;
+  if (!pt_stream_host || !pt_time_host)
+    return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_selfjoin_update: point arrays must be non-NULL");
+  // affected windows of every point: t - m + 1 .. t, merged into sorted runs per stream
+  std::vector<std::pair<int32_t, int32_t>> iv;
+  iv.reserve(n_pts);
+  for (int32_t u = 0; u < n_pts; ++u) {
+    const int32_t q = pt_stream_host[u], t = pt_time_host[u];
+    if (q < 0 || q >= n_streams || t < 0 || t >= stream_len_host[q])
+      return tsk_fail(ctx, TSK_ERR_INVALID_ARG, "mp_selfjoin_update: point %d (%d, %d) out of range", u, q, t);
+    iv.push_back({q, t});
+  }
+  std::sort(iv.begin(), iv.end());
+  std::vector<int4> runs;
+  std::vector<uint8_t> mask(n_streams, 0);
+  size_t tiles_max = 0;
+  for (const auto& p : iv) {
+    const int32_t q = p.first;
+    const int32_t l = stream_len_host[q] - m + 1;
+    const int32_t a = std::max(0, p.second - m + 1), b = std::min(l, p.second + 1);
+    if (a >= b) continue;
+    mask[q] = 1;
+    if (!runs.empty() && runs.back().x == q && a <= runs.back().z) {
+      runs.back().z = std::max(runs.back().z, b);
+    } else {
+      runs.push_back(make_int4(q, a, b, 0));
+      tiles_max += 2 * static_cast<size_t>((std::max(0, l - excl) + tsk_mp_band_width() - 1) / tsk_mp_band_width());
+    }
+  }
+  if (runs.empty()) return TSK_OK;
+  tsk_mp_plan plan;
+  if ((st = mp_plan(ctx, n_streams, stream_len_host, mask.data(), m, excl, TSK_MP_FP32, &plan))) return st;
+  if ((st = tsk_ws_require(ctx, tsk_mp_update_ws_bytes(plan, n_streams, runs.size(), tiles_max)))) return st;
+  return tsk_run_mp_update(ctx, X, n_streams, stream_len_host, plan, m, excl, P, I, runs, static_cast<char*>(ctx->ws));
+}
+
 extern "C" TSK_API tsk_status mp_abjoin(tsk_ctx* ctx, const void* A, const void* B, int32_t x_dtype, int32_t n_pairs,
                                         const int32_t* len_a_host, const int32_t* len_b_host, int32_t m,
                                         int32_t precision, void* P_a, int32_t* I_a, void* P_b, int32_t* I_b) {

@@ -202,6 +202,13 @@ tsk_status tsk_run_mp_ab(tsk_ctx* ctx, const void* A, const void* B, int x_dtype
                          const tsk_mp_plan& plan, int32_t m, int32_t precision, void* P_a, int32_t* I_a, void* P_b,
                          int32_t* I_b, char* ws);
 size_t tsk_mp_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams);
+// Incremental self-join profile after point updates: `runs` lists the affected
+// windows {stream, first, end, 0} (sorted, disjoint); P, I hold the old profile
+// on entry, the new one on return.  The plan's mask marks the touched streams.
+tsk_status tsk_run_mp_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int32_t* lens,
+                             const tsk_mp_plan& plan, int32_t m, int32_t excl, float* P, int32_t* I,
+                             const std::vector<int4>& runs, char* ws);
+size_t tsk_mp_update_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams, size_t n_runs, size_t n_tiles_max);
 int tsk_mp_band_width();
 // Aggregation and ranked discords.
 tsk_status tsk_launch_topk(tsk_ctx* ctx, const void* P, int p_dtype, const int32_t* I, int32_t n_series,

@@ -70,6 +70,15 @@ constexpr int kPad = 2048;               // zeroed slack after each stream's win
 constexpr float kEmpty = -3.0f;          // below every key (keys are rho - 1 >= -2)
 constexpr float kKeyFloor = -2.5f;       // keys above this are real cells
 constexpr double kConstRelVar = 1e-12;
+constexpr int kCand = 4;                 // near-tie candidate groups kept per window
+// Two groups whose float32 keys differ by at most this much (in rho) are near
+// ties: the recurrence's rounding (~1e-6 over the longest walks) may order them
+// either way, so both are re-scored exactly.
+constexpr float kNearTie = 3e-5f;
+// Near ties only matter for close matches: with keys within 1e-6 of each other
+// the 1e-3 bar on the distance binds once 1 - rho is below ~5e-3.  Groups with
+// keys below -kCloseKey go straight to the maximum (no candidate list).
+constexpr float kCloseKey = 0.02f;
 
 struct WinArrays {
   double* mu;
@@ -77,9 +86,11 @@ struct WinArrays {
   float* inv;
   float* df;
   float* dg;
-  unsigned long long* best;
+  unsigned long long* best;   // packed (key, first window of the best candidate group)
   int32_t* nxt;
   int32_t* constcnt;
+  int32_t* ncnt;              // near-tie groups offered per window (may exceed kCand)
+  unsigned long long* near;   // [window][kCand] near-tie groups, packed like best
   double* inv64;   // float64 mode only
   int32_t* bidx;   // float64 mode only
 };
@@ -237,16 +248,23 @@ __global__ void __launch_bounds__(kWinThreads) k_next_const(const int32_t* __res
 // t walks two groups of 8 diagonals, d0 + 8t + v (half a) and the same + 256
 // (half b); the two halves advance in lockstep, so every quantity of a cell
 // comes as a float2 pair (half a, half b) and the arithmetic runs as paired
-// float32 FMA/MUL.  Per row the lane's 8 + 8 cells update
-//   - the row maximum (one key per half, reduced over lanes in shared memory
-//     every 32 rows), and
-//   - 8 + 8 column maxima held in registers; as the rows advance the band's
-//     columns slide, the column leaving lane t passes to lane t-1 and the one
-//     leaving lane 0 is complete for this band.
-// A key is rho - 1 (one FMA: t * inv_i - 1, exact to float32 relative
-// precision near rho = 1, where close matches are told apart) with its 8 low
-// mantissa bits replaced by the diagonal's offset within its half (8t + v), so
-// maxima carry their argmax; the tag then costs at most 2^-16 of 1 - rho.
+// float32 FMA/MUL.  A cell's key is rho - 1 (one FMA: t * inv_i - 1, exact to
+// float32 relative precision near rho = 1, where close matches are told apart).
+// Per row the lane's 8 + 8 cells update
+//   - the row maximum: the maximum of each half's 8 keys, tagged with the lane
+//     (its 8 low mantissa bits), reduced over lanes in shared memory every 32
+//     rows, and
+//   - 8 + 8 column maxima held in registers: a column spends 8 rows in a lane
+//     (one slot); its maximum there is tagged with the lane when it leaves for
+//     lane t-1 and merged with the maximum it brought from the lanes above;
+//     lane 0's is complete for this band.
+// A maximum therefore names a group of 8 candidate windows (one lane's 8
+// diagonals, or the 8 rows a column spends in one lane), not one cell: tags
+// cost one operation per reduced maximum instead of one per cell.  Results
+// merge into a packed (key, first window of the group) 64-bit word per window
+// with atomicMax; a group that loses by at most kNearTie (or is displaced by
+// one at most kNearTie better) is kept as a near-tie candidate.  The
+// refinement re-scores the groups exactly.
 // Column data (df, dg, 1/norm) stream through a padded shared-memory ring
 // refilled 32 rows ahead; row data through a 32-row buffer of broadcast pairs.
 // Every per-row shared-memory access is a fixed offset from a per-block base.
@@ -270,8 +288,10 @@ struct MpArgs {
 struct __align__(16) MpWarpSmem {
   float2 ring[3][kRingPhys];      // column pairs (half a, half b), slot ring_phys(entry)
   float4 rrow[2][3][kChunk / 2];  // row broadcast pairs (v_s, v_s, v_s+1, v_s+1), double buffered
-  float2 rowbuf[32][kChunk + 1];  // (row key half a, half b): [lane][step], rows padded by one slot
+  float rowbuf[32][kChunk + 1];   // row maximum of both halves (tag: lane + 32 half): [lane][step]
   float2 colbuf[kChunk];          // keys of the columns leaving lane 0, per step
+  float2 inbuf[kVh][32];          // [slot][lane]: the slot's column maximum over the lanes above
+                                  // (each lane reads and writes only its own entries)
 };
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
@@ -285,6 +305,59 @@ __device__ __forceinline__ float tag_key(float rho, unsigned tag) {
   return __uint_as_float((__float_as_uint(rho) & 0xffffff00u) | tag);
 }
 __device__ __forceinline__ float untag_key(float key) { return __uint_as_float(__float_as_uint(key) & 0xffffff00u); }
+__device__ __forceinline__ int key_lane(float key) { return static_cast<int>(__float_as_uint(key) & 0x1fu); }
+// the float key of a packed (key, index) word
+__device__ __forceinline__ float packed_key(unsigned long long pk) {
+  const uint32_t u = static_cast<uint32_t>(pk >> 32);
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Per-window results of one side (row or column) of a tile.
+struct GroupOut {
+  unsigned long long* best;
+  int32_t* ncnt;
+  unsigned long long* near;
+};
+__device__ __forceinline__ GroupOut group_out(const WinArrays& wa, int64_t wb) {
+  return GroupOut{wa.best + wb, wa.ncnt + wb, wa.near + wb * kCand};
+}
+// Merge candidate group pk into window w's maximum (returns the previous one).
+__device__ __forceinline__ unsigned long long offer_max(const GroupOut& o, int w, unsigned long long pk) {
+  return atomicMax(&o.best[w], pk);
+}
+// Whichever of pk and the previous maximum `old` lost is kept as a near-tie
+// candidate when its key is within kNearTie of the winner's: every group within
+// kNearTie of the final maximum is then either the maximum or was offered to
+// the list.  A full list keeps its kCand largest entries.
+__device__ __noinline__ void offer_near(const GroupOut& o, int w, unsigned long long pk, unsigned long long old) {
+  const unsigned long long lo = old < pk ? old : pk;
+  if (lo == 0ull) return;
+  const unsigned long long hi = old < pk ? pk : old;
+  if (packed_key(lo) < packed_key(hi) - kNearTie) return;
+  unsigned long long* slot = o.near + static_cast<int64_t>(w) * kCand;
+  const int s = atomicAdd(&o.ncnt[w], 1);
+  if (s < kCand) {
+    slot[s] = lo;
+    return;
+  }
+  // full: replace the smallest entry if lo is larger (a few tries under contention)
+  for (int tries = 0; tries < kCand; ++tries) {
+    int at = 0;
+    unsigned long long mn = ~0ull;
+    for (int c = 0; c < kCand; ++c) {
+      const unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(slot + c);
+      if (v < mn) {
+        mn = v;
+        at = c;
+      }
+    }
+    if (mn >= lo || atomicCAS(slot + at, mn, lo) == mn) return;
+  }
+}
+__device__ __forceinline__ void offer(const GroupOut& o, int w, unsigned long long pk) {
+  offer_near(o, w, pk, offer_max(o, w, pk));
+}
+
 __device__ __forceinline__ float max3f(float a, float b, float c) {
   float r;
   asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -302,33 +375,38 @@ __device__ __forceinline__ double ld_guard(const TX* __restrict__ x, int idx, in
   return idx < n ? static_cast<double>(x[idx]) : 0.0;
 }
 
-// Merge the 32 (or `count`) buffered rows and lane-0 column exits into the profile.
-// Buffer step u belongs to row base + u and to columns base + u + d0 (+ 256).
-__device__ __forceinline__ void flush_chunk(MpWarpSmem& w, int count, int base, int d0, int l,
-                                            unsigned long long* __restrict__ best,
-                                            unsigned long long* __restrict__ bestc, int lane) {
+// Merge the 32 buffered rows and lane-0 column exits into the profile.  Buffer
+// step u belongs to row base + u and to columns base + u + d0 (+ 256).  A row
+// maximum from lane t' names the group of columns row + d0 (+ 256) + 8 t' + v;
+// a column maximum from lane t' the group of rows base + u - 8 t' - 7 + v
+// (v = 0 .. 7, either half).
+__device__ __forceinline__ void flush_chunk(MpWarpSmem& w, int base, int d0, int l, const GroupOut& rows,
+                                            const GroupOut& cols, int lane) {
   __syncwarp();
-  if (lane < count) {
-    const int ir = base + lane;
-    float ma = kEmpty, mb = kEmpty;
+  const int ir = base + lane;
+  float bk = kEmpty;
 #pragma unroll
-    for (int u = 0; u < 32; u += 2) {  // row `lane` of the chunk, from every source lane u
-      const float2 q0 = w.rowbuf[u][lane], q1 = w.rowbuf[u + 1][lane];
-      ma = max3f(ma, q0.x, q1.x);
-      mb = max3f(mb, q0.y, q1.y);
-    }
-    const bool useb = mb > ma;
-    const float bk = useb ? mb : ma;
-    if (bk > kKeyFloor) {
-      const int col = ir + d0 + (useb ? kHalf : 0) + static_cast<int>(__float_as_uint(bk) & 0xffu);
-      atomicMax(&best[ir], tsk_pack(untag_key(bk), col));
-    }
-    const float2 ck = w.colbuf[lane];
-    const int ja = ir + d0;
-    if (ck.x > kKeyFloor && ja < l)
-      atomicMax(&bestc[ja], tsk_pack(untag_key(ck.x), ir - static_cast<int>(__float_as_uint(ck.x) & 0xffu)));
-    if (ck.y > kKeyFloor && ja + kHalf < l)
-      atomicMax(&bestc[ja + kHalf], tsk_pack(untag_key(ck.y), ir - static_cast<int>(__float_as_uint(ck.y) & 0xffu)));
+  for (int u = 0; u < 32; u += 2) bk = max3f(bk, w.rowbuf[u][lane], w.rowbuf[u + 1][lane]);  // row `lane`, every source lane u
+  const float2 ck = w.colbuf[lane];
+  const int ja = ir + d0;
+  // the three merges are issued before any result is used (one round trip)
+  const int tg = static_cast<int>(__float_as_uint(bk) & 0x3fu);  // source lane + 32 half
+  const bool vr = bk > kKeyFloor, va = ck.x > kKeyFloor && ja < l, vb = ck.y > kKeyFloor && ja + kHalf < l;
+  const unsigned long long pr = tsk_pack(untag_key(bk), ir + d0 + (tg >> 5) * kHalf + kVh * (tg & 31));
+  const unsigned long long pa = tsk_pack(untag_key(ck.x), ir - kVh * key_lane(ck.x) - (kVh - 1));
+  const unsigned long long pb = tsk_pack(untag_key(ck.y), ir - kVh * key_lane(ck.y) - (kVh - 1));
+  const bool cr = vr && bk > -kCloseKey, ca = va && ck.x > -kCloseKey, cb = vb && ck.y > -kCloseKey;
+  if (cr || ca || cb) {
+    const unsigned long long orr = vr ? offer_max(rows, ir, pr) : 0ull;
+    const unsigned long long oa = va ? offer_max(cols, ja, pa) : 0ull;
+    const unsigned long long ob = vb ? offer_max(cols, ja + kHalf, pb) : 0ull;
+    if (cr) offer_near(rows, ir, pr, orr);
+    if (ca) offer_near(cols, ja, pa, oa);
+    if (cb) offer_near(cols, ja + kHalf, pb, ob);
+  } else {  // no close match: the results are not needed (fire and forget)
+    if (vr) atomicMax(&rows.best[ir], pr);
+    if (va) atomicMax(&cols.best[ja], pa);
+    if (vb) atomicMax(&cols.best[ja + kHalf], pb);
   }
   __syncwarp();
 }
@@ -343,11 +421,10 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
   const float* __restrict__ inv = a.wa.inv + wb;
   const float* __restrict__ df = a.wa.df + wb;
   const float* __restrict__ dg = a.wa.dg + wb;
-  unsigned long long* __restrict__ best = a.wa.best + wb;
   const float* __restrict__ invc = AB ? a.wa.inv + wbc : inv;
   const float* __restrict__ dfc = AB ? a.wa.df + wbc : df;
   const float* __restrict__ dgc = AB ? a.wa.dg + wbc : dg;
-  unsigned long long* __restrict__ bestc = AB ? a.wa.best + wbc : best;
+  const GroupOut rows = group_out(a.wa, wb), cols = group_out(a.wa, AB ? wbc : wb);
   const int m = a.m;
   const int dA = d0 + lane * kVh;  // first diagonal of half a (half b: + kHalf)
   const float2 kMinusOne2 = make_float2(-1.f, -1.f);
@@ -448,10 +525,12 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
     for (int v = 0; v < kVh; ++v) cov2[v] = make_float2(static_cast<float>(accA[v]), static_cast<float>(accB[v]));
   }
 
-  // ---- column state for the first row: slot v <-> columns r0 + dA + v (a) and + 256 (b)
+  // ---- column state for the first row: slot v <-> columns r0 + dA + v (a) and + 256 (b);
+  // ck: the column's maximum over this lane's rows so far (untagged), in: its
+  // maximum over the lanes above (tagged with the lane it came from)
   float2 cdf2[kVh], cdg2[kVh], cinv2[kVh];
   float ckA[kVh], ckB[kVh];
-  unsigned tagv[kVh];
+  const unsigned ltag = static_cast<unsigned>(lane), ltagb = ltag | 32u;
 #pragma unroll
   for (int v = 0; v < kVh; ++v) {
     const int j = r0 + dA + v;
@@ -460,7 +539,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
     cinv2[v] = make_float2(invc[j], invc[j + kHalf]);
     ckA[v] = kEmpty;
     ckB[v] = kEmpty;
-    tagv[v] = static_cast<unsigned>(lane * kVh + v);
+    w.inbuf[v][lane] = make_float2(kEmpty, kEmpty);
   }
 
   // ---- column ring: entry e <-> columns r0 + d0 + e (a) and + 256 (b)
@@ -520,7 +599,7 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
     // a multiple of 8): consecutive slots from ring_phys(ering)
     const float2* ringb = &w.ring[0][ring_phys(ering)];
     ering = (ering + kVh == kRingEntries) ? 0 : ering + kVh;
-    float2* rowp = &w.rowbuf[lane][sb];
+    float* rowp = &w.rowbuf[lane][sb];
     // keys of one row (slot c = (v + sr) % 8 holds the column of diagonal v), with
     // the covariance advanced to the next row
     auto row_keys = [&](int sr, int i, float2 rdf2, float2 rdg2, float2 rinv2, float (&kA)[kVh],
@@ -530,8 +609,8 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
         const int c = (v + sr) & (kVh - 1);
         const float2 t = __fmul2_rn(cov2[v], cinv2[c]);
         const float2 r = __ffma2_rn(t, rinv2, kMinusOne2);  // rho - 1: full relative precision near rho = 1
-        float ka = tag_key(r.x, tagv[v]);
-        float kb = tag_key(r.y, tagv[v]);
+        float ka = r.x;
+        float kb = r.y;
         if (MASKED) {
           const bool rowok = i < rEnd;
           ka = (rowok && i + dA + v < l) ? ka : kEmpty;
@@ -539,21 +618,24 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
         }
         kA[v] = ka;
         kB[v] = kb;
-        cov2[v] = __ffma2_rn(rdf2, cdg2[c], cov2[v]);
+        cov2[v] = __ffma2_rn(cdg2[c], rdf2, cov2[v]);
         cov2[v] = __ffma2_rn(cdf2[c], rdg2, cov2[v]);
       }
       const float rka = fmaxf(max3f(max3f(max3f(kA[0], kA[1], kA[2]), kA[3], kA[4]), kA[5], kA[6]), kA[7]);
       const float rkb = fmaxf(max3f(max3f(max3f(kB[0], kB[1], kB[2]), kB[3], kB[4]), kB[5], kB[6]), kB[7]);
-      rowp[sr] = make_float2(rka, rkb);
+      rowp[sr] = fmaxf(tag_key(rka, ltag), tag_key(rkb, ltagb));
     };
-    // the column in slot c0 leaves the lane (to lane - 1; lane 0's is complete for
-    // this band) and the column entering from the ring takes its place
-    auto exit_column = [&](int sr, int s, float la, float lb) {
-      const float ia = __shfl_down_sync(TSK_FULL_MASK, la, 1);
-      const float ib = __shfl_down_sync(TSK_FULL_MASK, lb, 1);
-      if (lane == 0) w.colbuf[s] = make_float2(la, lb);
-      ckA[sr] = (lane == 31) ? kEmpty : ia;
-      ckB[sr] = (lane == 31) ? kEmpty : ib;
+    // the column in slot sr leaves the lane with its maximum over this lane's
+    // rows (la, lb; tagged here) merged with the one it brought from above; it
+    // goes to lane - 1 (lane 0's is complete for this band) and the column
+    // entering from the ring takes the slot
+    auto exit_column = [&](int sr, int s, float la, float lb, float2 in) {
+      const float oa = fmaxf(in.x, tag_key(la, ltag));
+      const float ob = fmaxf(in.y, tag_key(lb, ltag));
+      const float ia = __shfl_down_sync(TSK_FULL_MASK, oa, 1);
+      const float ib = __shfl_down_sync(TSK_FULL_MASK, ob, 1);
+      if (lane == 0) w.colbuf[s] = make_float2(oa, ob);
+      w.inbuf[sr][lane] = make_float2((lane == 31) ? kEmpty : ia, (lane == 31) ? kEmpty : ib);
       cdf2[sr] = ringb[sr];
       cdg2[sr] = ringb[kRingPhys + sr];
       cinv2[sr] = ringb[2 * kRingPhys + sr];
@@ -567,38 +649,55 @@ __device__ __forceinline__ void mp_tile(const MpArgs& a, const TX* __restrict__ 
       // of row s0 and of diagonal (c - s0 - 1) % 8 of row s0 + 1
       const int s0 = 2 * gg;
       const int i0 = r0 + S0 + sb + s0;
+      // maxima over the lanes above of the two columns leaving this group's rows
+      // (stored by this lane when they arrived, 8 rows ago), read ahead of use
+      const float2 inS0 = w.inbuf[s0][lane], inS1 = w.inbuf[s0 + 1][lane];
       float k0A[kVh], k0B[kVh], k1A[kVh], k1B[kVh];
       row_keys(s0, i0, make_float2(rf4.x, rf4.y), make_float2(rg4.x, rg4.y), make_float2(ri4.x, ri4.y), k0A, k0B);
       // slot s0 leaves after row s0: its last key is diagonal 0 of row s0
-      exit_column(s0, sb + s0, fmaxf(ckA[s0], k0A[0]), fmaxf(ckB[s0], k0B[0]));
+      exit_column(s0, sb + s0, fmaxf(ckA[s0], k0A[0]), fmaxf(ckB[s0], k0B[0]), inS0);
       row_keys(s0 + 1, i0 + 1, make_float2(rf4.z, rf4.w), make_float2(rg4.z, rg4.w), make_float2(ri4.z, ri4.w),
                k1A, k1B);
 #pragma unroll
       for (int c = 0; c < kVh; ++c) {
         if (c == s0) {  // the column that entered after row s0 has only row s0 + 1's key (diagonal 7)
-          ckA[c] = fmaxf(ckA[c], k1A[kVh - 1]);
-          ckB[c] = fmaxf(ckB[c], k1B[kVh - 1]);
+          ckA[c] = k1A[kVh - 1];
+          ckB[c] = k1B[kVh - 1];
+        } else if (c == ((s0 + kVh - 1) & (kVh - 1))) {  // entered after row s0 - 1: diagonals 7, 6
+          ckA[c] = fmaxf(k0A[kVh - 1], k1A[kVh - 2]);
+          ckB[c] = fmaxf(k0B[kVh - 1], k1B[kVh - 2]);
         } else {
           ckA[c] = max3f(ckA[c], k0A[(c - s0) & (kVh - 1)], k1A[(c - s0 - 1) & (kVh - 1)]);
           ckB[c] = max3f(ckB[c], k0B[(c - s0) & (kVh - 1)], k1B[(c - s0 - 1) & (kVh - 1)]);
         }
       }
-      exit_column(s0 + 1, sb + s0 + 1, ckA[s0 + 1], ckB[s0 + 1]);
+      exit_column(s0 + 1, sb + s0 + 1, ckA[s0 + 1], ckB[s0 + 1], inS1);
     }
     }
-    flush_chunk(w, kChunk, r0 + S0, d0, l, best, bestc, lane);
+    flush_chunk(w, r0 + S0, d0, l, rows, cols, lane);
   }
   cp_async_wait_all();
   __syncwarp();
-  // columns still inside the band: slot v <-> columns r0 + nsteps + dA + v (+ 256)
+  // columns still inside the band: slot v <-> columns r0 + nsteps + dA + v (+ 256).
+  // The walk ends after an 8-row block, whose last row sent slot 7's column on:
+  // the column now in slot 7 has no rows in this lane yet.
+  ckA[kVh - 1] = kEmpty;
+  ckB[kVh - 1] = kEmpty;
 #pragma unroll
   for (int v = 0; v < kVh; ++v) {
     const int j = r0 + nsteps + dA + v;
-    const int row0 = r0 + nsteps + lane * kVh + v;  // = j - d0
-    if (ckA[v] > kKeyFloor && j < l)
-      atomicMax(&bestc[j], tsk_pack(untag_key(ckA[v]), row0 - static_cast<int>(__float_as_uint(ckA[v]) & 0xffu)));
-    if (ckB[v] > kKeyFloor && j + kHalf < l)
-      atomicMax(&bestc[j + kHalf], tsk_pack(untag_key(ckB[v]), row0 - static_cast<int>(__float_as_uint(ckB[v]) & 0xffu)));
+    const int row0 = r0 + nsteps + lane * kVh + v - (kVh - 1);  // = j - d0 - 7
+    const float2 in = w.inbuf[v][lane];
+    const float fa = fmaxf(in.x, tag_key(ckA[v], ltag));
+    const float fb = fmaxf(in.y, tag_key(ckB[v], ltag));
+    if (fa > kKeyFloor && j < l) {
+      const unsigned long long pk = tsk_pack(untag_key(fa), row0 - kVh * key_lane(fa));
+      if (fa > -kCloseKey) offer(cols, j, pk); else atomicMax(&cols.best[j], pk);
+    }
+    if (fb > kKeyFloor && j + kHalf < l) {
+      const unsigned long long pk = tsk_pack(untag_key(fb), row0 - kVh * key_lane(fb));
+      if (fb > -kCloseKey) offer(cols, j + kHalf, pk); else atomicMax(&cols.best[j + kHalf], pk);
+    }
   }
 }
 
@@ -724,8 +823,100 @@ __global__ void __launch_bounds__(128) k_mp_diag_f64(MpArgs a, int pass) {
 }
 
 // ---------------------------------------------------------------------------
-// 4. refinement: exact distance to each window's chosen neighbour
+// 4. refinement: exact distance to each window's nearest candidate
+//
+// The diagonal kernel names groups of 8 consecutive candidate windows of the
+// partner stream: the window's maximum's group and its near-tie groups.  Each
+// group's windows are scored with float32 sliding dot products of the centred
+// query window (c = sum_t a_t (y_t - ref) - (mean_j - ref) sum_t a_t, the
+// anchors' algebra), the group's best is re-scored exactly
+// (compensated sums), and the exact best over the groups is the neighbour
+// (lowest index on ties).  Constant candidates are left to the
+// constant-window rule.
 // ---------------------------------------------------------------------------
+template <typename TX>
+struct GroupScan;
+
+template <>
+struct GroupScan<float> {
+  // best admissible window of group [p, p + 8) for window i (-1 if none)
+  static __device__ int best(const float* __restrict__ x, int i, const float* __restrict__ xp, int p, int m,
+                             double mu_i, const double* __restrict__ mup, const float* __restrict__ invp, int lp,
+                             int excl, bool ab, float* key = nullptr) {
+    const float mih = static_cast<float>(mu_i), mil = static_cast<float>(mu_i - static_cast<double>(mih));
+    const int pc = max(p, 0);
+    const float ref = xp[pc];
+    float acc[kVh], win[kVh];
+#pragma unroll
+    for (int v = 0; v < kVh; ++v) {
+      acc[v] = 0.f;
+      const int q = p + v;
+      win[v] = (q >= 0 && q < lp + m - 1) ? __fsub_rn(xp[q], ref) : 0.f;
+    }
+    // win[s & 7] holds sample p + s (shifted by ref) for the 8 samples in use
+    const int np = lp + m - 1;
+    float sa = 0.f;
+    int t0 = 0;
+    for (; t0 + kVh <= m; t0 += kVh) {
+#pragma unroll
+      for (int u = 0; u < kVh; ++u) {
+        const float at = __fsub_rn(__fsub_rn(x[i + t0 + u], mih), mil);
+        sa = __fadd_rn(sa, at);
+#pragma unroll
+        for (int v = 0; v < kVh; ++v) acc[v] = __fmaf_rn(at, win[(v + u) & (kVh - 1)], acc[v]);
+        const int q = p + t0 + u + kVh;  // replaces sample p + t0 + u, no longer used
+        win[u] = (q >= 0 && q < np) ? __fsub_rn(xp[q], ref) : 0.f;
+      }
+    }
+    for (int t = t0; t < m; ++t) {
+      const float at = __fsub_rn(__fsub_rn(x[i + t], mih), mil);
+      sa = __fadd_rn(sa, at);
+#pragma unroll
+      for (int v = 0; v < kVh; ++v) {
+        const int q = p + v + t;
+        acc[v] = __fmaf_rn(at, (q >= 0 && q < np) ? __fsub_rn(xp[q], ref) : 0.f, acc[v]);
+      }
+    }
+    int bj = -1;
+    float bk = 0.f;
+#pragma unroll
+    for (int v = 0; v < kVh; ++v) {
+      const int j = p + v;
+      if (j < 0 || j >= lp || (!ab && abs(i - j) < excl) || invp[j] == 0.f) continue;
+      const float c = acc[v] - static_cast<float>(mup[j] - static_cast<double>(ref)) * sa;
+      const float k = c * invp[j];  // rho * norm_i: same scale for every candidate of window i
+      if (bj < 0 || k > bk) {
+        bj = j;
+        bk = k;
+      }
+    }
+    if (key) *key = bk;
+    return bj;
+  }
+};
+
+template <>
+struct GroupScan<double> {
+  static __device__ int best(const double* __restrict__ x, int i, const double* __restrict__ xp, int p, int m,
+                             double mu_i, const double* __restrict__ mup, const float* __restrict__ invp, int lp,
+                             int excl, bool ab) {
+    int bj = -1;
+    double bk = 0.0;
+    for (int v = 0; v < kVh; ++v) {
+      const int j = p + v;
+      if (j < 0 || j >= lp || (!ab && abs(i - j) < excl) || invp[j] == 0.f) continue;
+      double c = 0.0;
+      for (int t = 0; t < m; ++t) c = fma(x[i + t] - mu_i, xp[j + t], c);
+      const double k = c * static_cast<double>(invp[j]);
+      if (bj < 0 || k > bk) {
+        bj = j;
+        bk = k;
+      }
+    }
+    return bj;
+  }
+};
+
 template <typename TX, typename TP, bool AB>
 __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, const TX* __restrict__ X2, int split,
                                                    const int64_t* __restrict__ xoff,
@@ -783,20 +974,48 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
     return;
   }
   int j = -1;
+  double dist = INFINITY;
   if (exact64) {
     const int b = wa.bidx[wb + i];  // initialised to 0x7f7f7f7f (no neighbour)
     j = (b >= lp) ? -1 : b;
+    if (j >= 0) {
+      if (wa.inv[wbp + j] == 0.f) {
+        dist = sqm;
+      } else {
+        const double rho = tsk::window_rho(x, i, xp, j, m, wa.mu[wb + i], wa.mu[wbp + j]);
+        dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - rho)));
+      }
+    }
   } else {
-    const unsigned long long pk = wa.best[wb + i];
-    j = pk ? tsk_unpack_idx(pk) : -1;
-  }
-  double dist = INFINITY;
-  if (j >= 0) {
-    if (wa.inv[wbp + j] == 0.f) {
-      dist = sqm;
-    } else {
-      const double rho = tsk::window_rho(x, i, xp, j, m, wa.mu[wb + i], wa.mu[wbp + j]);
-      dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - rho)));
+    const int64_t wi = wb + i;
+    const unsigned long long pk = wa.best[wi];
+    if (pk) {
+      // the maximum's group and the near-tie groups within kNearTie of it
+      int grp[1 + kCand];
+      int ng = 0;
+      grp[ng++] = tsk_unpack_idx(pk);
+      const float k0 = packed_key(pk);
+      const int nc = min(wa.ncnt[wi], kCand);
+      for (int c = 0; c < nc; ++c) {
+        const unsigned long long q = wa.near[wi * kCand + c];
+        const int g = tsk_unpack_idx(q);
+        bool dup = packed_key(q) < k0 - kNearTie;
+        for (int e = 0; e < ng; ++e) dup |= grp[e] == g;
+        if (!dup) grp[ng++] = g;
+      }
+      const double* mup = wa.mu + wbp;
+      const float* invp = wa.inv + wbp;
+      double best_rho = -2.0;
+      for (int e = 0; e < ng; ++e) {
+        const int jg = GroupScan<TX>::best(x, i, xp, grp[e], m, wa.mu[wb + i], mup, invp, lp, excl, AB);
+        if (jg < 0) continue;
+        const double rho = tsk::window_rho(x, i, xp, jg, m, wa.mu[wb + i], mup[jg]);
+        if (rho > best_rho || (rho == best_rho && jg < j)) {
+          best_rho = rho;
+          j = jg;
+        }
+      }
+      if (j >= 0) dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - best_rho)));
     }
   }
   if (jc >= 0 && (sqm < dist || (sqm == dist && jc < j))) { dist = sqm; j = jc; }
@@ -846,6 +1065,10 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
   wa.best = cv.take<unsigned long long>(W);
   wa.nxt = cv.take<int32_t>(W);
   wa.constcnt = cv.take<int32_t>(n_streams);
+  if (!f64) {
+    wa.ncnt = cv.take<int32_t>(W);
+    wa.near = cv.take<unsigned long long>(W * kCand);
+  }
   unsigned long long* counter = cv.take<unsigned long long>(1);
   if (f64) {
     wa.inv64 = cv.take<double>(W);
@@ -854,6 +1077,7 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
   cudaStream_t st = ctx->stream;
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.best, 0, sizeof(unsigned long long) * W, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.constcnt, 0, sizeof(int32_t) * n_streams, st));
+  if (!f64) TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.ncnt, 0, sizeof(int32_t) * W, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   if (f64) TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.bidx, 0x7f, sizeof(int32_t) * W, st));  // ~INT_MAX
   if (plan.total_chunks > 0) {
@@ -933,6 +1157,199 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
   return TSK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// 5. incremental profile after point updates (Sec. III-C point updates; the
+//    streaming use of Sec. III-B)
+//
+// A sample t that changes moves the windows t-m+1 .. t (the affected set A).
+// The distance of two windows outside A is unchanged, so for such a window i
+// whose old neighbour is also outside A the new profile value is
+//   min(old value, min over a in A of dist(i, a)),
+// a window of A needs its whole row, and a window outside A whose old
+// neighbour was in A (the set R) needs its whole row too.  The cells with a
+// window of A on either side come from the diagonal kernel on work units that
+// cover only those rows and columns (per band: the rows of A, and the rows
+// whose columns in that band meet A); R's rows from a direct scan in groups
+// of 8 windows.  The maxima start from the old values (or nothing, for A and
+// R), and the refinement re-scores the winning groups exactly.
+// ---------------------------------------------------------------------------
+__global__ void k_upd_mark(const int4* __restrict__ runs, int n_runs, const int64_t* __restrict__ woff,
+                           uint8_t* __restrict__ aflag) {
+  const int r = blockIdx.x;
+  if (r >= n_runs) return;
+  const int4 u = runs[r];  // {stream, first window, end window, 0}
+  for (int i = u.y + threadIdx.x; i < u.z; i += blockDim.x) aflag[woff[u.x] + i] = 1;
+}
+
+// Start each touched window's maximum from its old profile value, or empty
+// for A and R; R's windows are listed for the row scan.
+__global__ void k_upd_init(const int64_t* __restrict__ xoff, const int32_t* __restrict__ len,
+                           const uint8_t* __restrict__ smask, const int64_t* __restrict__ woff, int n_streams,
+                           int64_t total, int m, const float* __restrict__ P, const int32_t* __restrict__ I,
+                           const uint8_t* __restrict__ aflag, WinArrays wa, int2* __restrict__ rlist,
+                           unsigned long long* __restrict__ rcount) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int q = tsk_find_segment<int64_t>(xoff, n_streams, e);
+  if (!smask[q]) return;
+  const int l = len[q] - m + 1;
+  const int i = static_cast<int>(e - xoff[q]);
+  if (i >= l) return;
+  const int64_t w = woff[q] + i;
+  wa.ncnt[w] = 0;
+  unsigned long long pk = 0ull;
+  if (!aflag[w]) {
+    const int j = I[e];
+    if (j >= 0 && j < l && aflag[woff[q] + j]) {
+      const unsigned long long at = atomicAdd(rcount, 1ull);
+      rlist[at] = make_int2(q, i);
+    } else if (j >= 0 && j < l) {
+      // the old value as a key: rho - 1 = -P^2 / (2m); a constant neighbour as the
+      // diagonal kernel sees it (rho = 0), the constant-window rule restores it
+      const float p = P[e];
+      const float key = wa.inv[woff[q] + j] == 0.f ? -1.f : static_cast<float>(-(static_cast<double>(p) * p) / (2.0 * m));
+      pk = tsk_pack(key, j);
+    }
+  }
+  wa.best[w] = pk;
+}
+
+// Whole rows of the windows in R: one warp per window, lanes over groups of 8
+// candidates, every group's best offered (near ties kept).
+__global__ void __launch_bounds__(256) k_upd_rowscan(const float* __restrict__ X, const int64_t* __restrict__ xoff,
+                                                     const int32_t* __restrict__ len, const int64_t* __restrict__ woff,
+                                                     int m, int excl, WinArrays wa, const int2* __restrict__ rlist,
+                                                     const unsigned long long* __restrict__ rcount) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
+  const long long n = static_cast<long long>(*rcount);
+  for (long long r = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nwarps) {
+    const int2 qi = rlist[r];
+    const int q = qi.x, i = qi.y;
+    const int l = len[q] - m + 1;
+    const float* x = X + xoff[q];
+    const int64_t wb = woff[q];
+    const GroupOut o = group_out(wa, wb);
+    const float inv_i = wa.inv[wb + i];
+    for (int p = lane * kVh; p < l; p += 32 * kVh) {
+      float k = 0.f;
+      const int j = GroupScan<float>::best(x, i, x, p, m, wa.mu[wb + i], wa.mu + wb, wa.inv + wb, l, excl, false, &k);
+      if (j >= 0) offer(o, i, tsk_pack(k * inv_i - 1.f, p));
+    }
+  }
+}
+
+tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int32_t* lens, const tsk_mp_plan& plan,
+                      int32_t m, int32_t excl, float* P, int32_t* I, const std::vector<int4>& runs, char* ws) {
+  // work units of the diagonal kernel, all masked: per band, the rows of each
+  // affected run and the rows whose columns in that band meet it (one unit
+  // when the two overlap)
+  std::vector<int4> tiles;
+  for (const int4& u : runs) {
+    const int64_t l = static_cast<int64_t>(lens[u.x]) - m + 1;
+    for (int64_t d0 = excl; d0 < l; d0 += kBand) {
+      const int64_t top = l - d0;  // rows with a cell in this band
+      int64_t r0 = u.y, r1 = std::min<int64_t>(u.z, top);                                   // rows in the run
+      int64_t c0 = std::max<int64_t>(0, u.y - d0 - (kBand - 1)), c1 = std::min<int64_t>(u.z - d0, top);  // rows meeting it
+      auto add = [&](int64_t a, int64_t b) {
+        if (a < b)
+          tiles.push_back(make_int4(u.x, static_cast<int>(d0), static_cast<int>(a),
+                                    static_cast<int>(static_cast<uint32_t>(b) | 0x80000000u)));
+      };
+      if (r0 < r1 && c0 < c1 && c1 >= r0 && r1 >= c0) {
+        add(std::min(r0, c0), std::max(r1, c1));
+      } else {
+        add(c0, c1);
+        add(r0, r1);
+      }
+    }
+  }
+  tsk_carver cv(ws);
+  const int64_t W = plan.total_windows;
+  WinArrays wa{};
+  wa.mu = cv.take<double>(W);
+  wa.ss = cv.take<double>(W);
+  wa.inv = cv.take<float>(W);
+  wa.df = cv.take<float>(W);
+  wa.dg = cv.take<float>(W);
+  wa.best = cv.take<unsigned long long>(W);
+  wa.nxt = cv.take<int32_t>(W);
+  wa.constcnt = cv.take<int32_t>(n_streams);
+  wa.ncnt = cv.take<int32_t>(W);
+  wa.near = cv.take<unsigned long long>(W * kCand);
+  unsigned long long* counter = cv.take<unsigned long long>(2);  // diagonal-kernel claims, |R|
+  uint8_t* aflag = cv.take<uint8_t>(W);
+  int2* rlist = cv.take<int2>(W);
+  int4* d_runs = cv.take<int4>(runs.size());
+  int4* d_tiles = cv.take<int4>(std::max<size_t>(tiles.size(), 1));
+  cudaStream_t st = ctx->stream;
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(aflag, 0, static_cast<size_t>(W), st));
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.constcnt, 0, sizeof(int32_t) * n_streams, st));
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st));
+  // (copies from pageable memory return once staged, so the vectors may go out of scope)
+  TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_runs, runs.data(), sizeof(int4) * runs.size(), cudaMemcpyHostToDevice, st));
+  if (!tiles.empty())
+    TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, st));
+  if (plan.total_chunks > 0) {
+    const size_t smem = sizeof(double) * 2 * (kWinChunk + m + 2);
+    TSK_CUDA_TRY(ctx, set_smem_limit(k_window_stats<float>, ctx->device, static_cast<int>(smem), 0));
+    k_window_stats<float><<<static_cast<unsigned>(plan.total_chunks), kWinThreads, smem, st>>>(
+        X, X, n_streams, plan.xoff, plan.len, plan.woff, plan.chunk_prefix, n_streams, m, 0, wa, ctx->d_err);
+    TSK_LAUNCH_CHECK(ctx, "k_window_stats");
+    k_next_const<<<n_streams, kWinThreads, 0, st>>>(plan.len, plan.smask, plan.woff, m, wa);
+    TSK_LAUNCH_CHECK(ctx, "k_next_const");
+  }
+  k_upd_mark<<<static_cast<unsigned>(runs.size()), 256, 0, st>>>(d_runs, static_cast<int>(runs.size()), plan.woff, aflag);
+  TSK_LAUNCH_CHECK(ctx, "k_upd_mark");
+  const int64_t total = plan.total_samples;
+  const unsigned gs = static_cast<unsigned>((total + 255) / 256);
+  k_upd_init<<<gs, 256, 0, st>>>(plan.xoff, plan.len, plan.smask, plan.woff, n_streams, total, m, P, I, aflag, wa,
+                                 rlist, counter + 1);
+  TSK_LAUNCH_CHECK(ctx, "k_upd_init");
+  if (!tiles.empty()) {
+    MpArgs a{};
+    a.X = X;
+    a.X2 = X;
+    a.split = n_streams;
+    a.xoff = plan.xoff;
+    a.len = plan.len;
+    a.woff = plan.woff;
+    a.tiles = d_tiles;
+    a.counter = counter;
+    a.wa = wa;
+    a.total_tiles = static_cast<int64_t>(tiles.size());
+    a.n_streams = n_streams;
+    a.m = m;
+    a.excl = excl;
+    a.H = 0;
+    const size_t smem = sizeof(MpWarpSmem) * kWarps;
+    TSK_CUDA_TRY(ctx, set_smem_limit(k_mp_diag<float, false>, ctx->device, static_cast<int>(smem), 1));
+    int per_sm = 0;
+    TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mp_diag<float, false>, kWarps * 32, smem));
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>((a.total_tiles + kWarps - 1) / kWarps, static_cast<int64_t>(per_sm) * ctx->sm_count);
+    a.total_warps = static_cast<int>(grid) * kWarps;
+    k_mp_diag<float, false><<<static_cast<unsigned>(grid), kWarps * 32, smem, st>>>(a);
+    TSK_LAUNCH_CHECK(ctx, "k_mp_diag");
+  }
+  k_upd_rowscan<<<static_cast<unsigned>(ctx->sm_count * 4), 256, 0, st>>>(X, plan.xoff, plan.len, plan.woff, m, excl,
+                                                                           wa, rlist, counter + 1);
+  TSK_LAUNCH_CHECK(ctx, "k_upd_rowscan");
+  k_mp_refine<float, float, false><<<gs, 256, 0, st>>>(X, X, n_streams, plan.xoff, plan.len, plan.smask, plan.woff,
+                                                       n_streams, total, m, excl, 0, wa, P, I, nullptr, nullptr);
+  TSK_LAUNCH_CHECK(ctx, "k_mp_refine");
+  return TSK_OK;
+}
+
+size_t update_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams, size_t n_runs, size_t n_tiles_max) {
+  const size_t W = static_cast<size_t>(plan.total_windows);
+  return tsk_carver::bytes_for(W, 8) * 2 + tsk_carver::bytes_for(W, 4) * 3 + tsk_carver::bytes_for(W, 8) +
+         tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_streams, 4) + tsk_carver::bytes_for(W, 4) +
+         tsk_carver::bytes_for(W * kCand, 8) + tsk_carver::bytes_for(2, 8) + tsk_carver::bytes_for(W, 1) +
+         tsk_carver::bytes_for(W, 8) + tsk_carver::bytes_for(n_runs, 16) + tsk_carver::bytes_for(n_tiles_max, 16) +
+         4096;
+}
+
 }  // namespace
 
 int tsk_mp_band_width() { return kBand; }
@@ -945,7 +1362,10 @@ size_t tsk_mp_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams) {
   size_t b = 0;
   b += tsk_carver::bytes_for(W, 8) * 2 + tsk_carver::bytes_for(W, 4) * 3 + tsk_carver::bytes_for(W, 8) +
        tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_streams, 4) + tsk_carver::bytes_for(1, 8);
-  if (plan.prec == TSK_MP_FP64) b += tsk_carver::bytes_for(W, 8) + tsk_carver::bytes_for(W, 4);
+  if (plan.prec == TSK_MP_FP64)
+    b += tsk_carver::bytes_for(W, 8) + tsk_carver::bytes_for(W, 4);
+  else
+    b += tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(W * kCand, 8);
   return b + 4096;
 }
 
@@ -956,6 +1376,16 @@ tsk_status tsk_run_mp(tsk_ctx* ctx, const void* X, int x_dtype, int32_t n_stream
                              n_streams, plan, m, excl, precision, P, I, nullptr, nullptr, ws);
   return run_typed<float>(ctx, static_cast<const float*>(X), static_cast<const float*>(X), n_streams, false, n_streams,
                           plan, m, excl, precision, P, I, nullptr, nullptr, ws);
+}
+
+tsk_status tsk_run_mp_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int32_t* lens,
+                             const tsk_mp_plan& plan, int32_t m, int32_t excl, float* P, int32_t* I,
+                             const std::vector<int4>& runs, char* ws) {
+  return run_update(ctx, X, n_streams, lens, plan, m, excl, P, I, runs, ws);
+}
+
+size_t tsk_mp_update_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams, size_t n_runs, size_t n_tiles_max) {
+  return update_ws_bytes(plan, n_streams, n_runs, n_tiles_max);
 }
 
 tsk_status tsk_run_mp_ab(tsk_ctx* ctx, const void* A, const void* B, int x_dtype, int32_t n_pairs,
@@ -978,7 +1408,7 @@ tsk_status tsk_run_mp_ab(tsk_ctx* ctx, const void* A, const void* B, int x_dtype
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr size_t kStaticScratchBytes = size_t(3) << 20;  // 3 MiB on every device that loads the library
+constexpr size_t kStaticScratchBytes = size_t(6) << 20;  // 6 MiB on every device that loads the library
 constexpr int kStaticMaxWindows = 65536;                   // l = n - m + 1 at most
 constexpr int kStaticMaxDevices = 64;
 
@@ -988,7 +1418,9 @@ std::mutex g_static_mu;
 void* g_static_addr[kStaticMaxDevices] = {};
 
 // Per-device set-up: the scratch array's device address and the kernels'
-// shared-memory limits.  Runs on the first call on each device.
+// shared-memory limits (raised to the largest size this entry point uses,
+// through the same per-device cache as the context path, so neither path can
+// lower a limit the other relies on).  Runs on the first call on each device.
 tsk_status static_setup(int dev, void** out) {
   std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_addr[dev]) {
@@ -998,10 +1430,9 @@ tsk_status static_setup(int dev, void** out) {
       return TSK_ERR_CUDA;
     }
     const int win_smem = static_cast<int>(sizeof(double) * 2 * (kWinChunk + 4096 + 2));
-    if (cudaFuncSetAttribute(k_window_stats<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, win_smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_mp_diag<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sizeof(MpWarpSmem) * kWarps)) != cudaSuccess) {
+    if (set_smem_limit(k_window_stats<float>, dev, win_smem, 0) != cudaSuccess ||
+        set_smem_limit(k_mp_diag<float, false>, dev, static_cast<int>(sizeof(MpWarpSmem) * kWarps), 1) !=
+            cudaSuccess) {
       cudaGetLastError();
       return TSK_ERR_CUDA;
     }
@@ -1009,6 +1440,40 @@ tsk_status static_setup(int dev, void** out) {
   }
   *out = g_static_addr[dev];
   return TSK_OK;
+}
+
+// Layout words of the one stream, written by the device (no host copy).
+struct StaticHead {
+  int64_t xoff[2], woff[2], chunk_prefix[2];
+  int32_t len[1];
+  uint8_t smask[4];
+};
+
+// Interior work units of band b (diagonals excl + 512 b ..): rows [0, rint) in
+// runs of H; the band's triangular end is one masked unit.
+__host__ __device__ inline int64_t static_band_rint(int64_t l, int64_t d0) {
+  int64_t rint = l - d0 - (kBand - 1);
+  if (rint < 0) rint = 0;
+  return rint - rint % kChunk;
+}
+
+// One warp writes the layout words and the work list: the interior units of
+// every band in band order, then one band-end unit per band.
+__global__ void k_static_plan(StaticHead h, StaticHead* __restrict__ dh, int4* __restrict__ tiles, int l, int excl,
+                              int H, int bands) {
+  if (threadIdx.x == 0) *dh = h;
+  int64_t interior = 0;
+  for (int b = 0; b < bands; ++b) interior += (static_band_rint(l, excl + static_cast<int64_t>(b) * kBand) + H - 1) / H;
+  for (int b = threadIdx.x; b < bands; b += blockDim.x) {
+    int64_t at = 0;
+    for (int c = 0; c < b; ++c) at += (static_band_rint(l, excl + static_cast<int64_t>(c) * kBand) + H - 1) / H;
+    const int d0 = excl + b * kBand;
+    const int64_t rint = static_band_rint(l, d0);
+    for (int64_t r0 = 0; r0 < rint; r0 += H)
+      tiles[at++] = make_int4(0, d0, static_cast<int>(r0), static_cast<int>(r0 + H < rint ? r0 + H : rint));
+    tiles[interior + b] =
+        make_int4(0, d0, static_cast<int>(rint), static_cast<int>(static_cast<uint32_t>(l - d0) | 0x80000000u));
+  }
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -1029,33 +1494,20 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TSK_ERR_CUDA;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
-  // work list of the one stream: interior units of every band, then the band ends
+  // work list of the one stream (built on the device): interior units of every
+  // band, then the band ends
   const int64_t e = l - excl;
   const double cells = e > 0 ? static_cast<double>(e) * (e + 1) / 2 : 0.0;
   int32_t H = static_cast<int32_t>(std::min(8192.0, std::max(2048.0, cells / (sms * 12.0 * 64.0 * kBand))));
   H = (H + kChunk - 1) / kChunk * kChunk;
-  std::vector<int4> tiles, tri;
-  for (int64_t d0 = excl; d0 < l; d0 += kBand) {
-    const int64_t rows = l - d0;
-    int64_t rint = std::max<int64_t>(0, rows - (kBand - 1));
-    rint -= rint % kChunk;
-    for (int64_t r0 = 0; r0 < rint; r0 += H)
-      tiles.push_back(make_int4(0, static_cast<int>(d0), static_cast<int>(r0), static_cast<int>(std::min<int64_t>(r0 + H, rint))));
-    if (rows > rint)
-      tri.push_back(make_int4(0, static_cast<int>(d0), static_cast<int>(rint),
-                              static_cast<int>(static_cast<uint32_t>(rows) | 0x80000000u)));
-  }
-  tiles.insert(tiles.end(), tri.begin(), tri.end());
+  const int bands = l > excl ? static_cast<int>((l - excl + kBand - 1) / kBand) : 0;
+  int64_t n_tiles = bands;
+  for (int b = 0; b < bands; ++b) n_tiles += (static_band_rint(l, excl + static_cast<int64_t>(b) * kBand) + H - 1) / H;
 
   // carve the scratch array
   const int64_t W = (l + kPad + 3) & ~int64_t(3);
-  struct Head {
-    int64_t xoff[2], woff[2], chunk_prefix[2];
-    int32_t len[1];
-    uint8_t smask[4];
-  };
   size_t off = 0;
-  const size_t o_head = off; off = align256(off + sizeof(Head));
+  const size_t o_head = off; off = align256(off + sizeof(StaticHead));
   const size_t o_mu = off; off = align256(off + 8 * W);
   const size_t o_ss = off; off = align256(off + 8 * W);
   const size_t o_inv = off; off = align256(off + 4 * W);
@@ -1063,25 +1515,30 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   const size_t o_dg = off; off = align256(off + 4 * W);
   const size_t o_best = off; off = align256(off + 8 * W);
   const size_t o_nxt = off; off = align256(off + 4 * W);
+  const size_t o_ncnt = off; off = align256(off + 4 * W);
+  const size_t o_near = off; off = align256(off + 8 * kCand * W);
   const size_t o_small = off; off = align256(off + 64);  // constcnt, counter, error word
-  const size_t o_tiles = off; off = align256(off + sizeof(int4) * tiles.size());
+  const size_t o_tiles = off; off = align256(off + sizeof(int4) * n_tiles);
   if (off > kStaticScratchBytes) return TSK_ERR_INVALID_ARG;
   char* sb = static_cast<char*>(base);
-  Head h{};
+  StaticHead h{};
   h.xoff[1] = n;
   h.woff[1] = W;
   h.chunk_prefix[1] = (l + kWinChunk - 1) / kWinChunk;
   h.len[0] = n;
   h.smask[0] = 1;
-  if (cudaMemcpyAsync(sb + o_head, &h, sizeof(Head), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      (!tiles.empty() && cudaMemcpyAsync(sb + o_tiles, tiles.data(), sizeof(int4) * tiles.size(),
-                                         cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
-      cudaMemsetAsync(sb + o_best, 0, 8 * W, stream) != cudaSuccess ||
+  StaticHead* dh = reinterpret_cast<StaticHead*>(sb + o_head);
+  int4* tiles = reinterpret_cast<int4*>(sb + o_tiles);
+  // every launch is checked before the next is issued: a failed one ends the call
+  auto launched = []() { return cudaGetLastError() == cudaSuccess; };
+  if (cudaMemsetAsync(sb + o_best, 0, 8 * W, stream) != cudaSuccess ||
+      cudaMemsetAsync(sb + o_ncnt, 0, 4 * W, stream) != cudaSuccess ||
       cudaMemsetAsync(sb + o_small, 0, 64, stream) != cudaSuccess) {
     cudaGetLastError();
     return TSK_ERR_CUDA;
   }
-  const Head* dh = reinterpret_cast<const Head*>(sb + o_head);
+  k_static_plan<<<1, 32, 0, stream>>>(h, dh, tiles, static_cast<int>(l), excl, H, bands);
+  if (!launched()) return TSK_ERR_CUDA;
   WinArrays wa{};
   wa.mu = reinterpret_cast<double*>(sb + o_mu);
   wa.ss = reinterpret_cast<double*>(sb + o_ss);
@@ -1090,6 +1547,8 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   wa.dg = reinterpret_cast<float*>(sb + o_dg);
   wa.best = reinterpret_cast<unsigned long long*>(sb + o_best);
   wa.nxt = reinterpret_cast<int32_t*>(sb + o_nxt);
+  wa.ncnt = reinterpret_cast<int32_t*>(sb + o_ncnt);
+  wa.near = reinterpret_cast<unsigned long long*>(sb + o_near);
   wa.constcnt = reinterpret_cast<int32_t*>(sb + o_small);
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(sb + o_small + 8);
   int* err = reinterpret_cast<int*>(sb + o_small + 16);
@@ -1097,8 +1556,10 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   const size_t win_smem = sizeof(double) * 2 * (kWinChunk + m + 2);
   k_window_stats<float><<<static_cast<unsigned>(h.chunk_prefix[1]), kWinThreads, win_smem, stream>>>(
       X, X, 1, dh->xoff, dh->len, dh->woff, dh->chunk_prefix, 1, m, 0, wa, err);
+  if (!launched()) return TSK_ERR_CUDA;
   k_next_const<<<1, kWinThreads, 0, stream>>>(dh->len, dh->smask, dh->woff, m, wa);
-  if (!tiles.empty()) {
+  if (!launched()) return TSK_ERR_CUDA;
+  if (n_tiles > 0) {
     MpArgs a{};
     a.X = X;
     a.X2 = X;
@@ -1106,10 +1567,10 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
     a.xoff = dh->xoff;
     a.len = dh->len;
     a.woff = dh->woff;
-    a.tiles = reinterpret_cast<const int4*>(sb + o_tiles);
+    a.tiles = tiles;
     a.counter = counter;
     a.wa = wa;
-    a.total_tiles = static_cast<int64_t>(tiles.size());
+    a.total_tiles = n_tiles;
     a.n_streams = 1;
     a.m = m;
     a.excl = excl;
@@ -1124,9 +1585,10 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
     const int64_t grid = std::min<int64_t>((a.total_tiles + kWarps - 1) / kWarps, static_cast<int64_t>(per_sm) * sms);
     a.total_warps = static_cast<int>(grid) * kWarps;
     k_mp_diag<float, false><<<static_cast<unsigned>(grid), kWarps * 32, smem, stream>>>(a);
+    if (!launched()) return TSK_ERR_CUDA;
   }
   k_mp_refine<float, float, false><<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
       X, X, 1, dh->xoff, dh->len, dh->smask, dh->woff, 1, n, m, excl, 0, wa, P, I, nullptr, nullptr);
-  if (cudaGetLastError() != cudaSuccess) return TSK_ERR_CUDA;
+  if (!launched()) return TSK_ERR_CUDA;
   return TSK_OK;
 }

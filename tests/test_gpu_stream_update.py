@@ -1,0 +1,117 @@
+"""GPU parity of the incremental profile after point updates (Sec. III-C point
+updates, followed by the streaming use Sec. III-B names) against the oracle's
+whole profile of the updated streams (Def. 6)."""
+import numpy as np
+import pytest
+
+from oracle import tsk_oracle as o
+from paper_2311_03393_gb300 import synth
+
+from helpers import check_profile
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tsk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_03393_gb300 import build
+    build.build()
+    import paper_2311_03393_gb300 as t
+    return t
+
+
+def _pack(xs):
+    return torch.cat([torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)) for x in xs]).cuda()
+
+
+def _run(tsk, xs, m, excl, changes):
+    """Profile xs, apply changes {(stream, t): delta} on the device copy, update; return new P, I and streams."""
+    lens = [len(x) for x in xs]
+    X = _pack(xs)
+    P, I = tsk.mp_selfjoin(X, lens, m, excl)
+    before = (P.clone(), I.clone())
+    off = np.concatenate([[0], np.cumsum(lens)])
+    new = [x.astype(np.float32).copy() for x in xs]
+    for (q, t), dl in changes.items():
+        new[q][t] = np.float32(new[q][t] + dl)
+        X[int(off[q]) + t] = float(new[q][t])
+    tsk.mp_selfjoin_update(X, lens, m, P, I, list(changes), excl)
+    tsk.sync()
+    return new, P.cpu().numpy(), I.cpu().numpy(), before, off
+
+
+def test_update_matches_the_oracle_profile_of_the_updated_streams(tsk):
+    rng = np.random.default_rng(91)
+    m, excl = 64, 16
+    xs = [np.cumsum(rng.normal(size=n)) for n in (5000, 3000, 4100)]
+    changes = {(0, 1234): 4.0, (0, 1240): -2.5, (2, 3): 3.0, (2, 4099): -5.0, (2, 2000): 1.5, (2, 2100): 2.0}
+    new, P, I, before, off = _run(tsk, xs, m, excl, changes)
+    for q in (0, 2):
+        l = len(new[q]) - m + 1
+        check_profile(new[q].astype(np.float64), m, excl, P[off[q]:off[q] + l], I[off[q]:off[q] + l])
+    # a stream without points is left as it was
+    np.testing.assert_array_equal(P[off[1]:off[2]], before[0].cpu().numpy()[off[1]:off[2]])
+    np.testing.assert_array_equal(I[off[1]:off[2]], before[1].cpu().numpy()[off[1]:off[2]])
+
+
+def test_update_where_the_change_creates_and_removes_nearest_neighbours(tsk):
+    """A planted repeat is destroyed at one place and created at another: rows whose old neighbour
+    was in the changed windows must be re-scanned, rows near the new repeat must find it."""
+    rng = np.random.default_rng(92)
+    m, excl = 50, 12
+    n = 3000
+    x = np.cumsum(rng.normal(size=n))
+    x[2000:2000 + m] = x[500:500 + m] + 0.01 * rng.normal(size=m)  # near-repeat of window 500 at 2000
+    changes = {(0, 2000 + t): float(rng.normal()) * 3.0 for t in range(0, m, 7)}  # destroy it
+    changes[(0, 1200)] = 0.0  # a point that does not change anything
+    new, P, I, _, _ = _run(tsk, [x], m, excl, changes)
+    l = n - m + 1
+    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l])
+
+
+def test_update_of_sketch_streams_after_a_point_update_of_the_series(tsk):
+    """ts_sketch_point_update moves every sketch stream at t; the profiles follow incrementally."""
+    rng = np.random.default_rng(93)
+    d, k, n, m = 7, 3, 2500, 40
+    excl = synth.default_excl(m)
+    T = np.cumsum(rng.normal(size=(d, n)), axis=1).astype(np.float32)
+    R = synth.gaussian_R(d, k, 94)
+    Tt = torch.from_numpy(T.ravel()).cuda()
+    Rt = torch.from_numpy(R).cuda()
+    S, stats = tsk.ts_sketch_build(Tt, Rt, [n], d, precision="fp32")
+    P, I = tsk.mp_selfjoin(S, [n] * k, m, excl)
+    ups = [(0, 2, 700, 6.0), (0, 5, 701, -4.0), (0, 0, 2499, 3.0)]
+    tsk.ts_sketch_point_update(S, stats, Rt, [n], d, *zip(*ups), T=Tt, precision="fp32")
+    pts = [(g, t) for g in range(k) for (_, _, t, _) in ups]
+    tsk.mp_selfjoin_update(S, [n] * k, m, P, I, pts, excl)
+    tsk.sync()
+    Sn = S.cpu().numpy().astype(np.float64).reshape(k, n)
+    Pn, In = P.cpu().numpy().reshape(k, n), I.cpu().numpy().reshape(k, n)
+    l = n - m + 1
+    for g in range(k):
+        check_profile(Sn[g], m, excl, Pn[g, :l], In[g, :l])
+
+
+def test_update_with_constant_windows(tsk):
+    """Square waves (constant windows) and a change inside a flat stretch."""
+    m, excl = 32, 8
+    n = 2400
+    t = np.arange(n)
+    x = np.where((t // 300) % 2 == 0, 0.0, 1.0) + 0.0
+    x[1500:1510] += np.linspace(0, 1, 10)
+    changes = {(0, 620): 0.5, (0, 1505): -0.3}
+    new, P, I, _, _ = _run(tsk, [x], m, excl, changes)
+    l = n - m + 1
+    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l])
+
+
+def test_update_rejects_points_out_of_range(tsk):
+    X = torch.zeros(1000, device="cuda")
+    P, I = tsk.mp_selfjoin(torch.randn(1000, device="cuda"), [1000], 20)
+    with pytest.raises(Exception):
+        tsk.mp_selfjoin_update(X, [1000], 20, P, I, [(0, 1000)])
+    with pytest.raises(Exception):
+        tsk.mp_selfjoin_update(X, [1000], 20, P, I, [(1, 5)])
