@@ -13,7 +13,7 @@ The metric is matrix-profile cell-updates per second over the step (a cell is
 one unordered window pair (i, j), j - i >= excl); the step's parts are timed
 too, giving the sketched vs exact discord-mining times.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload water]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload traffic]
   python bench.py --impl reference ...     (the FP64 CPU oracle on host cores)
 """
 from __future__ import annotations
@@ -39,9 +39,10 @@ UNIT = "cell-updates/s"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of the k_mp_diag launches of one step, from one ncu
-# capture per workload (profiles/launches_water_bench.md); None where not taken.
-MP_DIAG_DRAM_BYTES = {"water": [13032960, 13201408, 85382912]}
+# DRAM bytes (read + write) per k_mp_diag launch of one step, from one ncu
+# capture of the benchmark (dram__bytes_read.sum + dram__bytes_write.sum, the
+# second warm-up step); None where not taken for the kernel as it stands.
+MP_DIAG_DRAM_BYTES = {}
 
 WORKLOADS = {
     # name: (synth workload index, top-K, description)
@@ -59,8 +60,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    p.add_argument("--workload", default="water", choices=list(WORKLOADS))
+    p.add_argument("--workload", default="traffic", choices=list(WORKLOADS))
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the timed oracle sample")
+    p.add_argument("--cpu-workers", type=int, default=0, help="oracle worker processes (0: every host core)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--graph", action="store_true", help="capture the step in a CUDA graph and replay it")
@@ -163,60 +165,178 @@ def build_workload(name: str, rank: int):
 # reference arm: the FP64 oracle on host cores
 # ---------------------------------------------------------------------------
 
-def oracle_sample(wl, seconds: float, rng_seed: int = 0):
-    """Time the oracle's profile rows of the sketched streams until `seconds` pass.
-
-    Returns (cells, elapsed, rows, description).  Cells count unordered pairs:
-    one oracle row evaluates every admissible j, i.e. two half-pairs per cell.
-    """
+def _oracle_rows_worker(job):
+    """One worker of the timed oracle sample: random profile rows until the deadline."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import tsk_oracle as o
-    T = max(wl.series, key=lambda a: a.shape[1])
+    S, m, excl, seed, deadline, fixed = job
+    k, n = S.shape
+    l = n - m + 1
+    rng = np.random.default_rng(seed)
+    out = []
+    half_pairs = 0
+    todo = list(fixed)
+    while todo or (deadline is not None and time.time() < deadline):
+        g, i = todo.pop() if todo else (int(rng.integers(0, k)), int(rng.integers(0, l)))
+        P, I = o.mp_rows(S[g], m, excl, [i])
+        lo, hi = max(0, i - excl + 1), min(l, i + excl)
+        half_pairs += l - (hi - lo)
+        out.append((g, i, float(P[0]), int(I[0])))
+    return half_pairs, out
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_sketch(wl):
+    """The oracle's bf16-matched sketch of the first series (Sec. III-A, Alg. 1)."""
+    from oracle import tsk_oracle as o
+    T = wl.series[0]
+    Tbar, _, _ = o.global_znorm(T)
+    return o.sketch(Tbar, wl.R, bf16=True)
+
+
+def oracle_sample(wl, seconds: float, workers: int = 0, rng_seed: int = 0, pool=None):
+    """Time the oracle: its sketch of the series, then random profile rows of the
+    sketch streams on `workers` host processes (spawn-started) until `seconds` pass.
+
+    Returns (cells, elapsed, rows, description, cores).  Cells count unordered
+    pairs: one oracle row evaluates every admissible j, i.e. two half-pairs per
+    cell.  `rows` lists (g, i, P, I) of every row evaluated.
+    """
+    import multiprocessing as mp
+    workers = workers or host_cores()
     m = wl.m
     excl = int(math.ceil(m / 4))
     t0 = time.perf_counter()
-    Tbar, _, _ = o.global_znorm(T)
-    S = o.sketch(Tbar, wl.R, bf16=True)
-    n = T.shape[1]
-    l = n - m + 1
-    rng = np.random.default_rng(rng_seed)
-    half_pairs = 0
-    rows = 0
-    while time.perf_counter() - t0 < seconds:
-        g = int(rng.integers(0, S.shape[0]))
-        i = int(rng.integers(0, l))
-        o.mp_rows(S[g], m, excl, [i])
-        lo, hi = max(0, i - excl + 1), min(l, i + excl)
-        half_pairs += l - (hi - lo)
-        rows += 1
+    S = oracle_sketch(wl)
+    k, n = S.shape
+    deadline = time.time() + max(0.0, seconds - (time.perf_counter() - t0))
+    jobs = [(S, m, excl, rng_seed * 1000 + w, deadline, ()) for w in range(workers)]
+    own = pool is None
+    pool = pool or mp.get_context("spawn").Pool(workers)
+    try:
+        res = pool.map(_oracle_rows_worker, jobs, chunksize=1)
+    finally:
+        if own:
+            pool.close()
+            pool.join()
     el = time.perf_counter() - t0
-    desc = (f"oracle (numpy float64) sketch of the whole series + {rows} random matrix-profile rows of the "
-            f"{S.shape[0]} sketch streams (n={n}, m={m}), {el:.1f} s")
-    return half_pairs / 2.0, el, rows, desc
+    half_pairs = sum(r[0] for r in res)
+    rows = [row for r in res for row in r[1]]
+    desc = (f"oracle (numpy float64) sketch of the whole series (one core) + {len(rows)} random matrix-profile rows "
+            f"of the {k} sketch streams (n={n}, m={m}) on {workers} worker processes, {el:.1f} s "
+            f"({cpu_model()}, {host_cores()} host cores)")
+    return half_pairs / 2.0, el, rows, desc, workers
+
+
+def oracle_rows(wl, S, picks, workers: int = 0):
+    """Oracle profile rows (g, i) of the sketch streams S, spread over worker processes (untimed)."""
+    import multiprocessing as mp
+    workers = max(1, min(workers or host_cores(), len(picks)))
+    m = wl.m
+    excl = int(math.ceil(m / 4))
+    jobs = [(S, m, excl, 0, None, tuple(picks[w::workers])) for w in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_rows_worker, jobs, chunksize=1)
+    return {(g, i): (P, I) for r in res for (g, i, P, I) in r[1]}
+
+
+def parity_summary(wl, S_ref, rows, P_gpu, I_gpu, top, K, workers: int = 0):
+    """Errors of the GPU's results against the float64 oracle at the rows it evaluated.
+
+    P_gpu, I_gpu: (k, n) profiles of the sketch streams; rows: (g, i, P_ref, I_ref).
+    The bar is |P - P_ref| <= 1e-3 max(P_ref, 1e-2 sqrt(2m)); indices are equal or
+    tied (the GPU's neighbour is within the bar of P_ref by the oracle's distance).
+    Each reported discord gets the oracle's aggregated score at its index (Def. 5)
+    and its margin over the best window the ranking excluded it against.
+    """
+    from oracle import tsk_oracle as o
+    m = wl.m
+    fl = 1e-2 * math.sqrt(2 * m)
+    rel, absb, ratio = [], [], []
+    mism = mism_untied = 0
+    for g, i, pr, ir in rows:
+        if not math.isfinite(pr):
+            continue
+        pg = float(P_gpu[g, i])
+        err = abs(pg - pr)
+        ratio.append(err / (1e-3 * max(pr, fl)))
+        (rel if pr >= fl else absb).append(err / pr if pr >= fl else err)
+        jg = int(I_gpu[g, i])
+        if jg != ir:
+            mism += 1
+            dij = o.window_distance(S_ref[g], i, jg, m) if jg >= 0 else math.inf
+            if abs(dij - pr) > 1e-3 * max(pr, fl):
+                mism_untied += 1
+    idx, grp, score = (np.asarray(t.cpu()).reshape(-1, K)[0] for t in top[:3])
+    A = P_gpu.max(axis=0)
+    A = np.where(np.isfinite(A), A, -np.inf)
+    picks = [(g, int(i)) for i in idx if i >= 0 for g in range(P_gpu.shape[0])]
+    ref = oracle_rows(wl, S_ref, picks, workers)
+    disc = []
+    masked = A.copy()
+    for r in range(K):
+        i = int(idx[r])
+        if i < 0:
+            break
+        a_ref = max(ref[(g, i)][0] for g in range(P_gpu.shape[0]))
+        lo, hi = max(0, i - m + 1), min(len(masked), i + m)
+        masked[lo:hi] = -np.inf
+        runner = float(masked.max())
+        disc.append({"rank": r, "idx": i, "grp": int(grp[r]), "score": float(score[r]), "oracle_score": a_ref,
+                     "rel_err": abs(float(score[r]) - a_ref) / a_ref,
+                     "margin": (float(score[r]) - runner) / float(score[r])})
+    return {"bar": "|P - P_ref| <= 1e-3 max(P_ref, 1e-2 sqrt(2m)); float64 oracle of the bf16-matched sketch",
+            "rows": len(ratio), "max_rel_err": max(rel) if rel else None,
+            "max_abs_err_below_floor": max(absb) if absb else None, "max_err_over_bar": max(ratio) if ratio else None,
+            "rows_over_bar": int(sum(1 for x in ratio if x > 1.0)), "nn_index_differs": mism,
+            "nn_index_differs_not_tied": mism_untied, "discords": disc}
 
 
 def run_reference(args):
+    import multiprocessing as mp
     from paper_2311_03393_gb300 import dist
     rank, _, ws = dist.world()
     if rank != 0:
         return 0
     wl, K, desc = build_workload(args.workload, 0)
-    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        oracle_sample(wl, per_step / 4)
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    workers = args.cpu_workers or host_cores()
     cells = el = 0.0
     descs = []
-    for s in range(args.steps):
-        c, e, _, d = oracle_sample(wl, per_step, rng_seed=s + 1)
-        cells += c
-        el += e
-        descs.append(d)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for _ in range(args.warmup):
+            oracle_sample(wl, per_step / 4, workers, pool=pool)
+        for s in range(args.steps):
+            c, e, _, d, _ = oracle_sample(wl, per_step, workers, rng_seed=s + 1, pool=pool)
+            cells += c
+            el += e
+            descs.append(d)
     value = cells / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "sample": "random profile rows per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": descs[0]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": descs[0]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -443,8 +563,14 @@ def run_gpu(args):
         line["speedup_exact_over_sketched"] = parts[3] / parts[0] if parts[0] > 0 else None
         line["sketched_mining_cells_per_s"] = cells_sketched / (parts[0] / 1000.0)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        c, el, rows, sdesc = oracle_sample(wl, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": c / el, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc}
+        c, el, rows, sdesc, cores = oracle_sample(wl, args.cpu_seconds, args.cpu_workers)
+        line["cpu_baseline"] = {"value": c / el, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
+        # the same oracle rows against the GPU's profile of the sketch streams
+        n0 = lens[0]
+        Pg = np.stack([bufs["s"][0][g * n0:(g + 1) * n0].cpu().numpy() for g in range(k)]).astype(np.float64)
+        Ig = np.stack([bufs["s"][1][g * n0:(g + 1) * n0].cpu().numpy() for g in range(k)])
+        top = tsk.discord_topk(bufs["s"][0], bufs["s"][1], lens, k, m, K)
+        line["parity"] = parity_summary(wl, oracle_sketch(wl), rows, Pg, Ig, top, K, args.cpu_workers)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
