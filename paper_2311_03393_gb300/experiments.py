@@ -18,6 +18,8 @@ drawn on the device (cumulative sums of N(0, 1) steps from a seeded torch
 generator).
 
   python -m paper_2311_03393_gb300.experiments --d 250 500 1000 --trials 20
+  python -m paper_2311_03393_gb300.experiments scores --d 1000 --trials 100
+  python -m paper_2311_03393_gb300.experiments update --workload 3 --points 1 10
   python -m paper_2311_03393_gb300.experiments sketch --d 1024 --n 100000 --k 16
   python -m paper_2311_03393_gb300.experiments dims --d 1024 --n 20000 --m 144 --k 16 --K 10
 """
@@ -52,10 +54,13 @@ def _timed(fn):
 
 
 def trial(d: int, n: int, m: int, k: int, seed: int, device, top_frac: float = 1e-4,
-          sketch_precision: str = "bf16", R=None) -> dict:
+          sketch_precision: str = "bf16", R=None, sample_all: int = 0) -> dict:
     """One trial: the sketched discord's rank among all exact (window, dimension) scores.
 
     R: the (d, k) sketch matrix; default a seeded count sketch (Alg. 1).
+    sample_all: also return that many exact scores of uniformly drawn
+    (window, dimension) pairs (the "all subsequences" set of the score
+    distributions).
     """
     excl = api.default_excl(m)
     T = random_walks_device(d, n, seed, device)
@@ -102,7 +107,15 @@ def trial(d: int, n: int, m: int, k: int, seed: int, device, top_frac: float = 1
     # the other reading of the ranked list: time indices by their multidimensional score (Def. 5)
     A = P.max(dim=0).values
     time_rank = int((A > A[i_star]).sum().item()) + 1
-    return {"i": i_star, "j": j_star, "score": float(P[j_star, i_star]), "rank": rank, "allowed": allowed,
+    extra = {}
+    if sample_all:
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed) + 17)
+        flat = P.reshape(-1)
+        pick = torch.randint(0, flat.numel(), (int(sample_all),), generator=g, device=device)
+        extra["all_sample"] = flat[pick].cpu().numpy().astype(np.float64).tolist()
+        extra["score_refined"] = float(P[j_star, i_ref])
+    return {**extra, "i": i_star, "j": j_star, "score": float(P[j_star, i_star]), "rank": rank, "allowed": allowed,
             "time_rank": time_rank, "time_top_frac": time_rank / l,
             "success": rank <= allowed, "i_refined": i_ref, "rank_refined": rank_ref,
             "success_refined": rank_ref <= allowed, "exact_i": int(ex["idx"][0, 0]),
@@ -135,6 +148,54 @@ def sketch_quality(d: int, n: int = 10000, m: int = 100, trials: int = 100, k: i
             "refine_ms": rf, "exact_ms": ex, "speedup": ex / sk if sk > 0 else None,
             "speedup_with_refinement": ex / (sk + rf) if sk + rf > 0 else None,
             "sketch_precision": sketch_precision}
+
+
+def _summary(v) -> dict:
+    v = np.asarray(v, dtype=np.float64)
+    q = np.quantile(v, [0.01, 0.05, 0.25, 0.5, 0.75, 0.95, 0.99])
+    return {"count": int(v.size), "mean": float(v.mean()), "std": float(v.std()),
+            "quantiles": {f"{p:g}": float(x) for p, x in zip([0.01, 0.05, 0.25, 0.5, 0.75, 0.95, 0.99], q)}}
+
+
+def score_distribution(d: int = 1000, n: int = 10000, m: int = 100, trials: int = 100, k: int | None = None,
+                       seed: int = synth.SEED_BASE, device=None, sample_all: int = 4096,
+                       sketch_precision: str = "bf16") -> dict:
+    """The discord-score distributions of Sec. IV's synthetic experiment (its density figure, d = 1000).
+
+    Three sets of exact discord scores (1NN distances, Def. 6) over the trials:
+    all subsequences (a uniform sample of (window, dimension) pairs per trial),
+    the exact discords (Def. 4 top-1 of the exact d-dimensional path) and the
+    sketched discords (the exact score of the (i*, j*) the sketched path
+    returns, before and after the refinement).  Reported as quantiles, with the
+    exact discords' distance from the sketched discords' mean in units of the
+    sketched discords' standard deviation (the statistic the paper quotes for
+    its real datasets), and each set's distance from the all-subsequence mean.
+    """
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    k = int(math.ceil(math.sqrt(d))) if k is None else int(k)
+    trial(d, n, m, k, seed + 999983, device, sketch_precision=sketch_precision)
+    rows = [trial(d, n, m, k, seed + 7919 * t, device, sketch_precision=sketch_precision, sample_all=sample_all)
+            for t in range(trials)]
+    allv = np.concatenate([r["all_sample"] for r in rows])
+    allv = allv[np.isfinite(allv)]
+    ex = np.array([r["exact_score"] for r in rows])
+    sk = np.array([r["score"] for r in rows])
+    rf = np.array([r["score_refined"] for r in rows])
+    sd_sk = float(sk.std()) or float("nan")
+    sd_rf = float(rf.std()) or float("nan")
+    return {"d": d, "n": n, "m": m, "k": k, "trials": trials, "sketch_precision": sketch_precision,
+            "all_subsequences": _summary(allv), "exact_discords": _summary(ex), "sketched_discords": _summary(sk),
+            "sketched_refined_discords": _summary(rf),
+            "exact_vs_sketched_sd": float((ex.mean() - sk.mean()) / sd_sk),
+            "exact_vs_refined_sd": float((ex.mean() - rf.mean()) / sd_rf),
+            "sketched_vs_all_sd": float((sk.mean() - allv.mean()) / allv.std()),
+            "exact_vs_all_sd": float((ex.mean() - allv.mean()) / allv.std()),
+            "sketched_over_exact": float(np.mean(sk / ex)),
+            "success_rate": float(np.mean([r["success"] for r in rows])),
+            "time_rank_median": float(np.median([r["time_rank"] for r in rows])),
+            "time_top_0.01pct_rate": float(np.mean([r["time_rank"] <= max(1, int(1e-4 * (n - m + 1)))
+                                                    for r in rows])),
+            "time_top_1pct_rate": float(np.mean([r["time_top_frac"] <= 0.01 for r in rows]))}
 
 
 def sketch_throughput(d: int, n: int, k: int, reps: int = 5, seed: int = synth.SEED_BASE, precision: str = "bf16",
@@ -196,6 +257,43 @@ def dims_throughput(d: int, n: int, m: int, k: int, K: int, reps: int = 5, seed:
             "tfma_per_s": fmas / (per / 1e3) / 1e12}
 
 
+def update_throughput(index: int = 3, points: int = 1, reps: int = 5, seed: int = synth.SEED_BASE,
+                      device=None) -> dict:
+    """Time the incremental profile after point updates against a full re-profile.
+
+    Workload `index`'s first series is sketched (bf16), its k sketch streams
+    profiled; then `points` samples of one dimension change (ts_sketch_point_update
+    moves every sketch stream at those times) and the profiles follow with
+    mp_selfjoin_update.  Reports both times (CUDA events) and the speedup.
+    """
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    wl = synth.workload(index, seed=seed + index)
+    T0 = wl.series[0]
+    d, n = T0.shape
+    m, k = wl.m, wl.k
+    excl = api.default_excl(m)
+    T = torch.from_numpy(np.ascontiguousarray(T0.ravel())).to(device)
+    R = torch.from_numpy(wl.R).to(device)
+    S, stats = api.ts_sketch_build(T, R, [n], d, precision="bf16")
+    lens = [n] * k
+    P, I = api.mp_selfjoin(S, lens, m, excl)
+    rng = np.random.default_rng(seed)
+    t_full, t_upd = [], []
+    for r in range(reps + 1):
+        ts = sorted(int(x) for x in rng.integers(0, n, points))
+        ups = [(0, int(rng.integers(0, d)), t, float(rng.normal())) for t in ts]
+        api.ts_sketch_point_update(S, stats, R, [n], d, *zip(*ups), T=T, precision="bf16")
+        pts = [(g, t) for g in range(k) for t in ts]
+        _, ms_u = _timed(lambda: api.mp_selfjoin_update(S, lens, m, P, I, pts, excl))
+        _, ms_f = _timed(lambda: api.mp_selfjoin(S, lens, m, excl))
+        if r:
+            t_upd.append(ms_u)
+            t_full.append(ms_f)
+    mu, mf = float(np.median(t_upd)), float(np.median(t_full))
+    return {"workload": wl.name, "streams": k, "n": n, "m": m, "points": points, "update_ms": mu, "full_ms": mf,
+            "speedup": mf / mu if mu > 0 else None}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd")
@@ -212,6 +310,16 @@ def main(argv=None):
     t.add_argument("--k", type=int, default=16)
     t.add_argument("--reps", type=int, default=5)
     t.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    e = sub.add_parser("scores", help="discord-score distributions (all, exact, sketched) at one d")
+    e.add_argument("--d", type=int, default=1000)
+    e.add_argument("--n", type=int, default=10000)
+    e.add_argument("--m", type=int, default=100)
+    e.add_argument("--trials", type=int, default=100)
+    e.add_argument("--seed", type=int, default=synth.SEED_BASE)
+    u = sub.add_parser("update", help="incremental profile after point updates vs a full re-profile")
+    u.add_argument("--workload", type=int, default=3)
+    u.add_argument("--points", type=int, nargs="+", default=[1, 10])
+    u.add_argument("--reps", type=int, default=5)
     a = sub.add_parser("dims", help="time of the Alg. 3 dimension scan on one series")
     a.add_argument("--d", type=int, default=1024)
     a.add_argument("--n", type=int, default=20000)
@@ -227,6 +335,13 @@ def main(argv=None):
     args = ap.parse_args(raw)
     if args.cmd == "sketch":
         print(json.dumps(sketch_throughput(args.d, args.n, args.k, args.reps, precision=args.precision)), flush=True)
+        return
+    if args.cmd == "scores":
+        print(json.dumps(score_distribution(args.d, args.n, args.m, args.trials, seed=args.seed)), flush=True)
+        return
+    if args.cmd == "update":
+        for p in args.points:
+            print(json.dumps(update_throughput(args.workload, p, args.reps)), flush=True)
         return
     if args.cmd == "dims":
         print(json.dumps(dims_throughput(args.d, args.n, args.m, args.k, args.K, args.reps)), flush=True)
