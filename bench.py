@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per k_mp_diag launch of one step, from one ncu
 # capture of the benchmark (dram__bytes_read.sum + dram__bytes_write.sum, the
 # second warm-up step); None where not taken for the kernel as it stands.
-MP_DIAG_DRAM_BYTES = {}
+MP_DIAG_DRAM_BYTES = {"traffic": [54876160, 54271488, 7299570688]}  # sketched, re-profile, exact (1024 streams)
 
 WORKLOADS = {
     # name: (synth workload index, top-K, description)
