@@ -775,6 +775,17 @@ extern "C" TSK_API tsk_status mp_selfjoin_update(tsk_ctx* ctx, const float* X, i
   if (runs.empty()) return TSK_OK;
   tsk_mp_plan plan;
   if ((st = mp_plan(ctx, n_streams, stream_len_host, mask.data(), m, excl, TSK_MP_FP32, &plan))) return st;
+  // Re-scanning a changed window's neighbours costs about 1/64 of a whole
+  // profile per window of A (measured on GB300: break-even near 1.5% of the
+  // windows changed); past that the touched streams are profiled whole.
+  int64_t changed = 0, windows = 0;
+  for (const int4& u : runs) changed += u.z - u.y;
+  for (int32_t q = 0; q < n_streams; ++q)
+    if (mask[q]) windows += stream_len_host[q] - m + 1;
+  if (changed * 64 > windows) {
+    if ((st = tsk_ws_require(ctx, tsk_mp_ws_bytes(plan, n_streams)))) return st;
+    return tsk_run_mp(ctx, X, TSK_F32, n_streams, plan, m, excl, TSK_MP_FP32, P, I, static_cast<char*>(ctx->ws));
+  }
   if ((st = tsk_ws_require(ctx, tsk_mp_update_ws_bytes(plan, n_streams, runs.size(), tiles_max)))) return st;
   return tsk_run_mp_update(ctx, X, n_streams, stream_len_host, plan, m, excl, P, I, runs, static_cast<char*>(ctx->ws));
 }

@@ -39,6 +39,7 @@
 // and column maxima the column side's.
 #include "tsk_internal.cuh"
 #include "tsk_rho.cuh"
+#include "tsk_tc.cuh"
 
 #include <algorithm>
 #include <cfloat>
@@ -354,6 +355,7 @@ __device__ __noinline__ void offer_near(const GroupOut& o, int w, unsigned long 
     if (mn >= lo || atomicCAS(slot + at, mn, lo) == mn) return;
   }
 }
+__device__ __forceinline__ unsigned long long umax64_mp(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 __device__ __forceinline__ void offer(const GroupOut& o, int w, unsigned long long pk) {
   offer_near(o, w, pk, offer_max(o, w, pk));
 }
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
                                                    const int64_t* __restrict__ woff, int n_streams, int64_t total, int m,
                                                    int excl, int exact64, WinArrays wa, TP* __restrict__ P,
                                                    int32_t* __restrict__ I, TP* __restrict__ P2,
-                                                   int32_t* __restrict__ I2) {
+                                                   int32_t* __restrict__ I2, int keep_old = 0) {
   const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= total) return;
   const int q = tsk_find_segment<int64_t>(xoff, n_streams, e);
@@ -989,6 +991,17 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
   } else {
     const int64_t wi = wb + i;
     const unsigned long long pk = wa.best[wi];
+    if (keep_old && pk && wa.ncnt[wi] == 0) {
+      // incremental update: a maximum still at the old value it started from (no
+      // group beat it or came near) keeps the old result, unless the
+      // constant-window rule now gives a nearer window
+      const int jo = Iout[eo];
+      const float po = static_cast<float>(Pout[eo]);
+      if (jo >= 0 && jo < lp) {
+        const float key = wa.inv[wbp + jo] == 0.f ? -1.f : static_cast<float>(-(static_cast<double>(po) * po) / (2.0 * m));
+        if (tsk_pack(key, jo) == pk && !(jc >= 0 && (sqm < po || (sqm == po && jc < jo)))) return;
+      }
+    }
     if (pk) {
       // the maximum's group and the near-tie groups within kNearTie of it
       int grp[1 + kCand];
@@ -1186,8 +1199,8 @@ __global__ void k_upd_mark(const int4* __restrict__ runs, int n_runs, const int6
 __global__ void k_upd_init(const int64_t* __restrict__ xoff, const int32_t* __restrict__ len,
                            const uint8_t* __restrict__ smask, const int64_t* __restrict__ woff, int n_streams,
                            int64_t total, int m, const float* __restrict__ P, const int32_t* __restrict__ I,
-                           const uint8_t* __restrict__ aflag, WinArrays wa, int2* __restrict__ rlist,
-                           unsigned long long* __restrict__ rcount) {
+                           const uint8_t* __restrict__ aflag, WinArrays wa, int32_t* __restrict__ rlist,
+                           int32_t* __restrict__ rcount) {
   const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= total) return;
   const int q = tsk_find_segment<int64_t>(xoff, n_streams, e);
@@ -1201,8 +1214,8 @@ __global__ void k_upd_init(const int64_t* __restrict__ xoff, const int32_t* __re
   if (!aflag[w]) {
     const int j = I[e];
     if (j >= 0 && j < l && aflag[woff[q] + j]) {
-      const unsigned long long at = atomicAdd(rcount, 1ull);
-      rlist[at] = make_int2(q, i);
+      const int at = atomicAdd(&rcount[q], 1);  // R of stream q: rlist[woff[q] + k]
+      rlist[woff[q] + at] = i;
     } else if (j >= 0 && j < l) {
       // the old value as a key: rho - 1 = -P^2 / (2m); a constant neighbour as the
       // diagonal kernel sees it (rho = 0), the constant-window rule restores it
@@ -1214,28 +1227,174 @@ __global__ void k_upd_init(const int64_t* __restrict__ xoff, const int32_t* __re
   wa.best[w] = pk;
 }
 
-// Whole rows of the windows in R: one warp per window, lanes over groups of 8
-// candidates, every group's best offered (near ties kept).
+// Whole rows of the windows in R on the FP32 pipe (m > 512): one warp per
+// window, lanes over groups of 8 candidates, every group's best offered (near
+// ties kept).
 __global__ void __launch_bounds__(256) k_upd_rowscan(const float* __restrict__ X, const int64_t* __restrict__ xoff,
                                                      const int32_t* __restrict__ len, const int64_t* __restrict__ woff,
-                                                     int m, int excl, WinArrays wa, const int2* __restrict__ rlist,
-                                                     const unsigned long long* __restrict__ rcount) {
+                                                     int n_streams, int m, int excl, WinArrays wa,
+                                                     const int32_t* __restrict__ rlist,
+                                                     const int32_t* __restrict__ rcount) {
   const int lane = threadIdx.x & 31;
-  const long long nwarps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
-  const long long n = static_cast<long long>(*rcount);
-  for (long long r = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nwarps) {
-    const int2 qi = rlist[r];
-    const int q = qi.x, i = qi.y;
+  const int nwarps = static_cast<int>(gridDim.x) * (blockDim.x >> 5);
+  const int wg = static_cast<int>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int q = 0; q < n_streams; ++q) {
+    const int nr = rcount[q];
     const int l = len[q] - m + 1;
     const float* x = X + xoff[q];
     const int64_t wb = woff[q];
     const GroupOut o = group_out(wa, wb);
-    const float inv_i = wa.inv[wb + i];
-    for (int p = lane * kVh; p < l; p += 32 * kVh) {
-      float k = 0.f;
-      const int j = GroupScan<float>::best(x, i, x, p, m, wa.mu[wb + i], wa.mu + wb, wa.inv + wb, l, excl, false, &k);
-      if (j >= 0) offer(o, i, tsk_pack(k * inv_i - 1.f, p));
+    for (int k = wg; k < nr; k += nwarps) {
+      const int i = rlist[wb + k];
+      const float inv_i = wa.inv[wb + i];
+      for (int p = lane * kVh; p < l; p += 32 * kVh) {
+        float key = 0.f;
+        const int j = GroupScan<float>::best(x, i, x, p, m, wa.mu[wb + i], wa.mu + wb, wa.inv + wb, l, excl, false, &key);
+        if (j >= 0) offer(o, i, tsk_pack(key * inv_i - 1.f, p));
+      }
     }
+  }
+}
+
+// Whole rows of the windows in R on the tensor cores (m <= 512): one CTA per
+// (stream, chunk of 1024 windows), the stream's R windows as queries in batches
+// of 16 against the chunk's Hankel matrix (tsk_tc.cuh); each query's best
+// window of the chunk is offered (near ties kept).
+constexpr int kUpdPairs = kWinChunk + tsk::kTcMaxKT * 16 + 32;
+
+size_t upd_tc_smem_bytes() {
+  return 2 * static_cast<size_t>(kUpdPairs) * sizeof(uint32_t) + 2 * static_cast<size_t>(kWinChunk) * sizeof(float) +
+         static_cast<size_t>(tsk::kTcMaxKT) * 2 * 32 * sizeof(uint4);
+}
+
+__global__ void __launch_bounds__(256, 2) k_upd_rowscan_tc(const float* __restrict__ X, const int64_t* __restrict__ xoff,
+                                                           const int32_t* __restrict__ len,
+                                                           const int64_t* __restrict__ woff,
+                                                           const int64_t* __restrict__ chunk_prefix, int n_streams,
+                                                           int64_t total_chunks, int m, int excl, WinArrays wa,
+                                                           const int32_t* __restrict__ rlist,
+                                                           const int32_t* __restrict__ rcount) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t* Hp = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* Lp = Hp + kUpdPairs;
+  float* wmean = reinterpret_cast<float*>(Lp + kUpdPairs);  // window mean - x_ref
+  float* winv = wmean + kWinChunk;
+  uint4* Bs = reinterpret_cast<uint4*>(winv + kWinChunk);
+  __shared__ float red[8];
+  __shared__ int qidx[16];
+  __shared__ float qscale[16], qsum[16], qinv[16], qmh[16], qml[16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int KT = (m + 15) >> 4;
+  for (int64_t item = blockIdx.x; item < total_chunks; item += gridDim.x) {
+    const int q = tsk_find_segment<int64_t>(chunk_prefix, n_streams, item);
+    const int nr = rcount[q];
+    if (nr == 0) continue;
+    const int l = len[q] - m + 1;
+    const int t0 = static_cast<int>(item - chunk_prefix[q]) * kWinChunk;
+    const int nw = min(kWinChunk, l - t0);
+    const float* xs = X + xoff[q];
+    const float* x = xs + t0;
+    const int64_t wb = woff[q];
+    const float x_ref = x[0];
+    const int ns = nw + m - 1;
+    // ---- stage the chunk: scale, (hi, lo) pairs, window means and inverse norms
+    float amax = 0.f;
+    for (int p = tid; p < ns; p += blockDim.x) amax = fmaxf(amax, fabsf(x[p] - x_ref));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(TSK_FULL_MASK, amax, o));
+    if (lane == 0) red[warp] = amax;
+    __syncthreads();
+    amax = 0.f;
+    for (int u = 0; u < 8; ++u) amax = fmaxf(amax, red[u]);
+    const float sx = tsk::pow2_scale(amax);
+    for (int p = tid; p < kUpdPairs; p += blockDim.x) {
+      __half h0 = __float2half_rn(0.f), l0 = h0, h1 = h0, l1 = h0;
+      if (p < ns) tsk::split_h((x[p] - x_ref) * sx, h0, l0);
+      if (p + 1 < ns) tsk::split_h((x[p + 1] - x_ref) * sx, h1, l1);
+      Hp[p] = tsk::h2_bits(h0, h1);
+      Lp[p] = tsk::h2_bits(l0, l1);
+    }
+    for (int w = tid; w < kWinChunk; w += blockDim.x) {
+      wmean[w] = w < nw ? static_cast<float>(wa.mu[wb + t0 + w] - static_cast<double>(x_ref)) : 0.f;
+      winv[w] = w < nw ? wa.inv[wb + t0 + w] : 0.f;
+    }
+    for (int b0 = 0; b0 < nr; b0 += 16) {
+      const int nb = min(16, nr - b0);
+      __syncthreads();  // staging done / the previous batch's fragments no longer read
+      // ---- the batch's queries: centred in float32 (two-term mean), their sum and scale
+      for (int r = warp; r < nb; r += 8) {
+        const int i = rlist[wb + b0 + r];
+        const double mu = wa.mu[wb + i];
+        const float mh = static_cast<float>(mu), ml = static_cast<float>(mu - static_cast<double>(mh));
+        float sum = 0.f;
+        for (int t = lane; t < m; t += 32) sum += __fsub_rn(__fsub_rn(xs[i + t], mh), ml);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(TSK_FULL_MASK, sum, o);
+        if (lane == 0) {
+          const float inv = wa.inv[wb + i];
+          qidx[r] = i;
+          qsum[r] = sum;
+          qinv[r] = inv;
+          qscale[r] = inv > 0.f ? 1.f / tsk::pow2_scale(1.f / inv) : 1.f;  // max |q| <= ||q|| < qscale
+          qmh[r] = mh;
+          qml[r] = ml;
+        }
+      }
+      __syncthreads();
+      const int NT = (nb + 7) >> 3;
+      for (int e = tid; e < KT * NT * 32; e += blockDim.x) {
+        const tsk::BEntry be = tsk::b_entry(e, NT);
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (be.slot < nb) {
+          const int i = qidx[be.slot];
+          const float sc = 1.f / qscale[be.slot];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = tsk::b_tap(be, u);
+            v[u] = t < m ? __fsub_rn(__fsub_rn(xs[i + t], qmh[be.slot]), qml[be.slot]) * sc : 0.f;
+          }
+        }
+        Bs[(be.kt * 2 + be.nt) * 32 + be.lane] = tsk::b_pack(v);
+      }
+      __syncthreads();
+      unsigned long long best[2][2] = {{0ull, 0ull}, {0ull, 0ull}};
+      for (int mt = warp; mt * 16 < nw; mt += 8) {
+        float c1[2][4], c2[2][4];
+        tsk::hankel_tile(Hp, Lp, Bs, mt * 16, KT, NT, lane, c1, c2);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int slot = nt * 8 + 2 * tq + cc;
+            if (nt >= NT || slot >= nb || qinv[slot] == 0.f) continue;
+            const int i = qidx[slot];
+            const float back = qscale[slot] / sx;
+#pragma unroll
+            for (int rh = 0; rh < 2; ++rh) {
+              const int w = mt * 16 + g + 8 * rh;
+              const int t = t0 + w;
+              if (w >= nw || abs(t - i) < excl || winv[w] == 0.f) continue;
+              const float acc = __fmaf_rn(c2[nt][2 * rh + cc], 0x1p-11f, c1[nt][2 * rh + cc]) * back;
+              const float cov = __fmaf_rn(-wmean[w], qsum[slot], acc);
+              const float key = fminf(0.f, fmaxf(-2.f, __fmaf_rn(cov * qinv[slot], winv[w], -1.f)));
+              best[nt][cc] = umax64_mp(best[nt][cc], tsk_pack(key, t));
+            }
+          }
+      }
+      const GroupOut o = group_out(wa, wb);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          unsigned long long bb = best[nt][cc];
+#pragma unroll
+          for (int sh = 4; sh < 32; sh <<= 1) bb = umax64_mp(bb, __shfl_xor_sync(TSK_FULL_MASK, bb, sh));
+          const int slot = nt * 8 + 2 * tq + cc;
+          if (g == 0 && slot < nb && bb) offer(o, qidx[slot], bb);
+        }
+    }
+    __syncthreads();  // shared buffers are reused by the next item
   }
 }
 
@@ -1277,15 +1436,17 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
   wa.constcnt = cv.take<int32_t>(n_streams);
   wa.ncnt = cv.take<int32_t>(W);
   wa.near = cv.take<unsigned long long>(W * kCand);
-  unsigned long long* counter = cv.take<unsigned long long>(2);  // diagonal-kernel claims, |R|
+  unsigned long long* counter = cv.take<unsigned long long>(1);  // diagonal-kernel claims
+  int32_t* rcount = cv.take<int32_t>(n_streams);                 // |R| per stream
   uint8_t* aflag = cv.take<uint8_t>(W);
-  int2* rlist = cv.take<int2>(W);
+  int32_t* rlist = cv.take<int32_t>(W);                          // R of stream q at woff[q]
   int4* d_runs = cv.take<int4>(runs.size());
   int4* d_tiles = cv.take<int4>(std::max<size_t>(tiles.size(), 1));
   cudaStream_t st = ctx->stream;
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(aflag, 0, static_cast<size_t>(W), st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.constcnt, 0, sizeof(int32_t) * n_streams, st));
-  TSK_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st));
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(rcount, 0, sizeof(int32_t) * n_streams, st));
   // (copies from pageable memory return once staged, so the vectors may go out of scope)
   TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_runs, runs.data(), sizeof(int4) * runs.size(), cudaMemcpyHostToDevice, st));
   if (!tiles.empty())
@@ -1304,7 +1465,7 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
   const int64_t total = plan.total_samples;
   const unsigned gs = static_cast<unsigned>((total + 255) / 256);
   k_upd_init<<<gs, 256, 0, st>>>(plan.xoff, plan.len, plan.smask, plan.woff, n_streams, total, m, P, I, aflag, wa,
-                                 rlist, counter + 1);
+                                 rlist, rcount);
   TSK_LAUNCH_CHECK(ctx, "k_upd_init");
   if (!tiles.empty()) {
     MpArgs a{};
@@ -1332,11 +1493,23 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
     k_mp_diag<float, false><<<static_cast<unsigned>(grid), kWarps * 32, smem, st>>>(a);
     TSK_LAUNCH_CHECK(ctx, "k_mp_diag");
   }
-  k_upd_rowscan<<<static_cast<unsigned>(ctx->sm_count * 4), 256, 0, st>>>(X, plan.xoff, plan.len, plan.woff, m, excl,
-                                                                           wa, rlist, counter + 1);
+  if (m <= tsk::kTcMaxKT * 16) {
+    const size_t smem = upd_tc_smem_bytes();
+    TSK_CUDA_TRY(ctx, set_smem_limit(k_upd_rowscan_tc, ctx->device, static_cast<int>(smem), 2));
+    int per_sm = 0;
+    TSK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_rowscan_tc, 256, smem));
+    const int64_t grid = std::min<int64_t>(std::max<int64_t>(plan.total_chunks, 1),
+                                           static_cast<int64_t>(std::max(per_sm, 1)) * ctx->sm_count);
+    k_upd_rowscan_tc<<<static_cast<unsigned>(grid), 256, smem, st>>>(X, plan.xoff, plan.len, plan.woff,
+                                                                      plan.chunk_prefix, n_streams, plan.total_chunks,
+                                                                      m, excl, wa, rlist, rcount);
+  } else {
+    k_upd_rowscan<<<static_cast<unsigned>(ctx->sm_count * 4), 256, 0, st>>>(X, plan.xoff, plan.len, plan.woff,
+                                                                             n_streams, m, excl, wa, rlist, rcount);
+  }
   TSK_LAUNCH_CHECK(ctx, "k_upd_rowscan");
   k_mp_refine<float, float, false><<<gs, 256, 0, st>>>(X, X, n_streams, plan.xoff, plan.len, plan.smask, plan.woff,
-                                                       n_streams, total, m, excl, 0, wa, P, I, nullptr, nullptr);
+                                                       n_streams, total, m, excl, 0, wa, P, I, nullptr, nullptr, 1);
   TSK_LAUNCH_CHECK(ctx, "k_mp_refine");
   return TSK_OK;
 }
@@ -1345,9 +1518,9 @@ size_t update_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams, size_t n_runs
   const size_t W = static_cast<size_t>(plan.total_windows);
   return tsk_carver::bytes_for(W, 8) * 2 + tsk_carver::bytes_for(W, 4) * 3 + tsk_carver::bytes_for(W, 8) +
          tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_streams, 4) + tsk_carver::bytes_for(W, 4) +
-         tsk_carver::bytes_for(W * kCand, 8) + tsk_carver::bytes_for(2, 8) + tsk_carver::bytes_for(W, 1) +
-         tsk_carver::bytes_for(W, 8) + tsk_carver::bytes_for(n_runs, 16) + tsk_carver::bytes_for(n_tiles_max, 16) +
-         4096;
+         tsk_carver::bytes_for(W * kCand, 8) + tsk_carver::bytes_for(1, 8) + tsk_carver::bytes_for(n_streams, 4) +
+         tsk_carver::bytes_for(W, 1) + tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_runs, 16) +
+         tsk_carver::bytes_for(n_tiles_max, 16) + 4096;
 }
 
 }  // namespace

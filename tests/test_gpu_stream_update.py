@@ -43,39 +43,60 @@ def _run(tsk, xs, m, excl, changes):
     return new, P.cpu().numpy(), I.cpu().numpy(), before, off
 
 
+def _rows(l, changes, q, m, stride=5):
+    """Rows to compare: every window near a change and a regular sample of the rest."""
+    near = [np.arange(max(0, t - 2 * m), min(l, t + m)) for (qq, t) in changes if qq == q]
+    return np.unique(np.concatenate(near + [np.arange(0, l, stride)]))
+
+
 def test_update_matches_the_oracle_profile_of_the_updated_streams(tsk):
+    """Few changed windows (< 1.5% of a stream): the incremental path."""
     rng = np.random.default_rng(91)
     m, excl = 64, 16
-    xs = [np.cumsum(rng.normal(size=n)) for n in (5000, 3000, 4100)]
-    changes = {(0, 1234): 4.0, (0, 1240): -2.5, (2, 3): 3.0, (2, 4099): -5.0, (2, 2000): 1.5, (2, 2100): 2.0}
+    xs = [np.cumsum(rng.normal(size=n)) for n in (16000, 3000, 14100)]
+    changes = {(0, 1234): 4.0, (0, 1240): -2.5, (2, 3): 3.0, (2, 14099): -5.0}
     new, P, I, before, off = _run(tsk, xs, m, excl, changes)
     for q in (0, 2):
         l = len(new[q]) - m + 1
-        check_profile(new[q].astype(np.float64), m, excl, P[off[q]:off[q] + l], I[off[q]:off[q] + l])
+        check_profile(new[q].astype(np.float64), m, excl, P[off[q]:off[q] + l], I[off[q]:off[q] + l],
+                      rows=_rows(l, changes, q, m))
     # a stream without points is left as it was
     np.testing.assert_array_equal(P[off[1]:off[2]], before[0].cpu().numpy()[off[1]:off[2]])
     np.testing.assert_array_equal(I[off[1]:off[2]], before[1].cpu().numpy()[off[1]:off[2]])
 
 
 def test_update_where_the_change_creates_and_removes_nearest_neighbours(tsk):
-    """A planted repeat is destroyed at one place and created at another: rows whose old neighbour
-    was in the changed windows must be re-scanned, rows near the new repeat must find it."""
+    """A planted near-repeat is destroyed: rows whose old neighbour was in the changed windows
+    must be re-scanned, and a zero change re-profiles its windows to the same values."""
     rng = np.random.default_rng(92)
     m, excl = 50, 12
-    n = 3000
+    n = 12000
     x = np.cumsum(rng.normal(size=n))
-    x[2000:2000 + m] = x[500:500 + m] + 0.01 * rng.normal(size=m)  # near-repeat of window 500 at 2000
-    changes = {(0, 2000 + t): float(rng.normal()) * 3.0 for t in range(0, m, 7)}  # destroy it
-    changes[(0, 1200)] = 0.0  # a point that does not change anything
+    x[9000:9000 + m] = x[500:500 + m] + 0.01 * rng.normal(size=m)  # near-repeat of window 500 at 9000
+    changes = {(0, 9000 + t): float(rng.normal()) * 3.0 for t in range(0, m, 7)}  # destroy it
+    changes[(0, 4200)] = 0.0  # a point that does not change anything
     new, P, I, _, _ = _run(tsk, [x], m, excl, changes)
     l = n - m + 1
-    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l])
+    rows = np.unique(np.concatenate([_rows(l, changes, 0, m, stride=7), np.arange(450, 560)]))
+    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l], rows=rows)
+
+
+def test_many_changes_take_the_whole_profile(tsk):
+    """Past ~1.5% changed windows the touched streams are profiled whole; same result."""
+    rng = np.random.default_rng(95)
+    m, excl = 40, 10
+    xs = [np.cumsum(rng.normal(size=n)) for n in (3000, 2500)]
+    changes = {(0, int(t)): float(rng.normal()) for t in rng.choice(3000, 40, replace=False)}
+    new, P, I, before, off = _run(tsk, xs, m, excl, changes)
+    l = len(new[0]) - m + 1
+    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l], rows=np.arange(0, l, 3))
+    np.testing.assert_array_equal(P[off[1]:off[2]], before[0].cpu().numpy()[off[1]:off[2]])
 
 
 def test_update_of_sketch_streams_after_a_point_update_of_the_series(tsk):
     """ts_sketch_point_update moves every sketch stream at t; the profiles follow incrementally."""
     rng = np.random.default_rng(93)
-    d, k, n, m = 7, 3, 2500, 40
+    d, k, n, m = 7, 3, 12000, 40
     excl = synth.default_excl(m)
     T = np.cumsum(rng.normal(size=(d, n)), axis=1).astype(np.float32)
     R = synth.gaussian_R(d, k, 94)
@@ -83,7 +104,7 @@ def test_update_of_sketch_streams_after_a_point_update_of_the_series(tsk):
     Rt = torch.from_numpy(R).cuda()
     S, stats = tsk.ts_sketch_build(Tt, Rt, [n], d, precision="fp32")
     P, I = tsk.mp_selfjoin(S, [n] * k, m, excl)
-    ups = [(0, 2, 700, 6.0), (0, 5, 701, -4.0), (0, 0, 2499, 3.0)]
+    ups = [(0, 2, 7000, 6.0), (0, 5, 7001, -4.0), (0, 0, n - 1, 3.0)]
     tsk.ts_sketch_point_update(S, stats, Rt, [n], d, *zip(*ups), T=Tt, precision="fp32")
     pts = [(g, t) for g in range(k) for (_, _, t, _) in ups]
     tsk.mp_selfjoin_update(S, [n] * k, m, P, I, pts, excl)
@@ -92,20 +113,21 @@ def test_update_of_sketch_streams_after_a_point_update_of_the_series(tsk):
     Pn, In = P.cpu().numpy().reshape(k, n), I.cpu().numpy().reshape(k, n)
     l = n - m + 1
     for g in range(k):
-        check_profile(Sn[g], m, excl, Pn[g, :l], In[g, :l])
+        check_profile(Sn[g], m, excl, Pn[g, :l], In[g, :l], rows=_rows(l, pts, g, m, stride=9))
 
 
 def test_update_with_constant_windows(tsk):
-    """Square waves (constant windows) and a change inside a flat stretch."""
+    """Square waves (constant windows), a change inside a flat stretch and one that makes a
+    window constant."""
     m, excl = 32, 8
-    n = 2400
+    n = 9000
     t = np.arange(n)
     x = np.where((t // 300) % 2 == 0, 0.0, 1.0) + 0.0
     x[1500:1510] += np.linspace(0, 1, 10)
     changes = {(0, 620): 0.5, (0, 1505): -0.3}
     new, P, I, _, _ = _run(tsk, [x], m, excl, changes)
     l = n - m + 1
-    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l])
+    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l], rows=_rows(l, changes, 0, m, stride=4))
 
 
 def test_update_rejects_points_out_of_range(tsk):
