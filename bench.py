@@ -176,7 +176,9 @@ def _oracle_rows_worker(job):
     out = []
     half_pairs = 0
     todo = list(fixed)
-    while todo or (deadline is not None and time.time() < deadline):
+    first = deadline is not None  # a timed worker evaluates at least one row
+    while todo or first or (deadline is not None and time.time() < deadline):
+        first = False
         g, i = todo.pop() if todo else (int(rng.integers(0, k)), int(rng.integers(0, l)))
         P, I = o.mp_rows(S[g], m, excl, [i])
         lo, hi = max(0, i - excl + 1), min(l, i + excl)
