@@ -90,6 +90,33 @@ def test_constant_windows_self_pair_and_no_train_profile(tsk):
     assert np.all(px <= MP_REL_TOL * d_floor(m) + 1e-2)
 
 
+def test_close_matches_in_both_directions(tsk):
+    """Noisy periodic test and training streams (joint period 850): every window has several
+    near-repeats in the other stream, within ~1e-6 of each other in rho and in different bands
+    or sides, so the choice among them rests on the near-tie candidates' exact re-scores."""
+    rng = np.random.default_rng(57)
+    m = 40
+
+    def stream(n, noise, phase):
+        t = np.arange(n) + phase
+        return (np.sin(2 * np.pi * t / 50) + 0.5 * np.sin(2 * np.pi * t / 17) + noise * rng.normal(size=n)
+                ).astype(np.float32)
+
+    A = [stream(4000, 0.01, 0), stream(2600, 0.02, 13)]
+    B = [stream(5000, 0.01, 300), stream(3500, 0.005, 7)]
+    la, lb = [len(x) for x in A], [len(x) for x in B]
+    P_a, I_a, P_b, I_b = tsk.mp_abjoin(_pack(A, torch.float32), _pack(B, torch.float32), la, lb, m,
+                                       train_profile=True)
+    tsk.sync()
+    P_a, I_a, P_b, I_b = (t.cpu().numpy() for t in (P_a, I_a, P_b, I_b))
+    oa = np.concatenate([[0], np.cumsum(la)])
+    ob = np.concatenate([[0], np.cumsum(lb)])
+    for q in range(2):
+        l_a, l_b = la[q] - m + 1, lb[q] - m + 1
+        _check_ab(A[q], B[q], m, P_a[oa[q]:oa[q] + l_a], I_a[oa[q]:oa[q] + l_a], rows=np.arange(0, l_a, 3))
+        _check_ab(B[q], A[q], m, P_b[ob[q]:ob[q] + l_b], I_b[ob[q]:ob[q] + l_b], rows=np.arange(0, l_b, 3))
+
+
 def test_sketched_and_exact_ab_discords_match_the_oracle(tsk):
     """Planted window in test only; bf16 sketch of train and test with one R, then Alg. 2 and Alg. 3."""
     d, n, m, k, K = 6, 2400, 40, 3, 3
