@@ -80,6 +80,10 @@ constexpr float kNearTie = 3e-5f;
 // the 1e-3 bar on the distance binds once 1 - rho is below ~5e-3.  Groups with
 // keys below -kCloseKey go straight to the maximum (no candidate list).
 constexpr float kCloseKey = 0.02f;
+// The refinement re-scores candidates exactly only where some float32
+// correlation reaches this; below it float32 (~1e-6 in rho) gives the distance
+// to ~1e-4 relative (dist error ~ drho / (2 (1 - rho))), a tenth of the 1e-3 bar.
+constexpr float kExactRho = 0.99f;
 
 struct WinArrays {
   double* mu;
@@ -901,7 +905,7 @@ template <>
 struct GroupScan<double> {
   static __device__ int best(const double* __restrict__ x, int i, const double* __restrict__ xp, int p, int m,
                              double mu_i, const double* __restrict__ mup, const float* __restrict__ invp, int lp,
-                             int excl, bool ab) {
+                             int excl, bool ab, float* key = nullptr) {
     int bj = -1;
     double bk = 0.0;
     for (int v = 0; v < kVh; ++v) {
@@ -915,6 +919,7 @@ struct GroupScan<double> {
         bk = k;
       }
     }
+    if (key) *key = static_cast<float>(bk);
     return bj;
   }
 };
@@ -1018,17 +1023,39 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
       }
       const double* mup = wa.mu + wbp;
       const float* invp = wa.inv + wbp;
-      double best_rho = -2.0;
+      // each group's best by float32 sliding dot products; correlations rho ~ key / ||x_i - mean||
+      int gj[1 + kCand];
+      float gr[1 + kCand];
+      int nv = 0;
+      float rmax = -2.f;
+      const float inv_i = wa.inv[wb + i];
       for (int e = 0; e < ng; ++e) {
-        const int jg = GroupScan<TX>::best(x, i, xp, grp[e], m, wa.mu[wb + i], mup, invp, lp, excl, AB);
+        float kg = 0.f;
+        const int jg = GroupScan<TX>::best(x, i, xp, grp[e], m, wa.mu[wb + i], mup, invp, lp, excl, AB, &kg);
         if (jg < 0) continue;
-        const double rho = tsk::window_rho(x, i, xp, jg, m, wa.mu[wb + i], mup[jg]);
-        if (rho > best_rho || (rho == best_rho && jg < j)) {
-          best_rho = rho;
-          j = jg;
+        gj[nv] = jg;
+        gr[nv] = kg * inv_i;
+        rmax = fmaxf(rmax, gr[nv]);
+        ++nv;
+      }
+      double best_rho = -2.0;
+      if (rmax < kExactRho) {
+        // no close match: float32 resolves rho to ~1e-6, 1e-5 of the distance
+        for (int e = 0; e < nv; ++e)
+          if (gr[e] > best_rho || (gr[e] == best_rho && gj[e] < j)) {
+            best_rho = gr[e];
+            j = gj[e];
+          }
+      } else {
+        for (int e = 0; e < nv; ++e) {
+          const double rho = tsk::window_rho(x, i, xp, gj[e], m, wa.mu[wb + i], mup[gj[e]]);
+          if (rho > best_rho || (rho == best_rho && gj[e] < j)) {
+            best_rho = rho;
+            j = gj[e];
+          }
         }
       }
-      if (j >= 0) dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - best_rho)));
+      if (j >= 0) dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, best_rho))));
     }
   }
   if (jc >= 0 && (sqm < dist || (sqm == dist && jc < j))) { dist = sqm; j = jc; }
