@@ -103,6 +103,13 @@ TSK_API tsk_status tsk_mp_workspace_bytes(tsk_ctx* ctx, int32_t n_streams, const
  * for its own asynchronous copies ran out (about a second; the results of the
  * calls since the last sync are then invalid). */
 TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s);
+/* Failure-path self-test: issues, on the context's stream, one block whose
+ * bounded device-side wait (the kind the sketch kernel uses for its own
+ * copies) waits on a barrier nothing completes.  It gives up after about a
+ * second and sets the device error word, so the next tsk_sync returns
+ * TSK_ERR_TIMEOUT; the context stays usable.  No fault, trap or unbounded
+ * wait is involved.  (Not a step of the paper's method.) */
+TSK_API tsk_status tsk_selftest_timeout(tsk_ctx* ctx);
 /* Rows per matrix-profile work unit (a band of 512 diagonals x `rows` rows):
  * 0 = automatic (about 64 units per resident warp, 2048..8192), else a
  * multiple of 32 in [32, 1 << 20].  Smaller units balance short streams,

@@ -34,6 +34,7 @@ SIGNATURES = {
     "tsk_reserve": (_I32, [_P, C.c_size_t]),
     "tsk_mp_workspace_bytes": (_I32, [_P, _I32, _P, _I32, C.POINTER(C.c_size_t)]),
     "tsk_sync": (_I32, [_P, C.c_double]),
+    "tsk_selftest_timeout": (_I32, [_P]),
     "tsk_set_tile_rows": (_I32, [_P, _I32]),
     "tsk_launch_count": (_I64, [_P]),
     "tsk_profile_enable": (_I32, [_P, _I32]),

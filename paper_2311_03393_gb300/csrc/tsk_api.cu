@@ -532,6 +532,12 @@ extern "C" TSK_API tsk_status tsk_set_tile_rows(tsk_ctx* ctx, int32_t rows) {
 
 extern "C" TSK_API int64_t tsk_launch_count(const tsk_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+extern "C" TSK_API tsk_status tsk_selftest_timeout(tsk_ctx* ctx) {
+  tsk_status st = enter(ctx);
+  if (st) return st;
+  return tsk_launch_selftest_wait(ctx);
+}
+
 extern "C" TSK_API tsk_status tsk_sync(tsk_ctx* ctx, double timeout_s) {
   tsk_status st = enter(ctx);
   if (st) return st;

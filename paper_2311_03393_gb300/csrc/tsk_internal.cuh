@@ -202,6 +202,8 @@ tsk_status tsk_run_mp_ab(tsk_ctx* ctx, const void* A, const void* B, int x_dtype
                          const tsk_mp_plan& plan, int32_t m, int32_t precision, void* P_a, int32_t* I_a, void* P_b,
                          int32_t* I_b, char* ws);
 size_t tsk_mp_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams);
+// One bounded device-side wait that runs out (failure-path self-test).
+tsk_status tsk_launch_selftest_wait(tsk_ctx* ctx);
 // Incremental self-join profile after point updates: `runs` lists the affected
 // windows {stream, first, end, 0} (sorted, disjoint); P, I hold the old profile
 // on entry, the new one on return.  The plan's mask marks the touched streams.

@@ -19,13 +19,18 @@
 //                       Each cell's key rho - 1 (rho = c * inv_i * inv_j) updates
 //                       the row maximum (reduced over lanes through shared memory)
 //                       and the column maximum (carried from lane to lane as the
-//                       band's columns slide).  Keys carry the diagonal's offset
-//                       within its half band in their 8 low mantissa bits, so a
-//                       max also knows its argmax.  Results merge into a packed
-//                       (key, index) 64-bit word per window with atomicMax.
-//   4. k_mp_refine      for every window: its chosen neighbour's distance,
-//                       dist = sqrt(2 m (1 - rho)) with rho re-evaluated exactly
-//                       (compensated sums), plus the constant-window rules.
+//                       band's columns slide).  Maxima are tagged once per lane
+//                       (8 low mantissa bits), so a maximum names a group of 8
+//                       candidate windows.  Results merge into a packed (key,
+//                       first window of the group) 64-bit word per window with
+//                       atomicMax; groups within kNearTie of a window's maximum
+//                       are kept as near-tie candidates.
+//   4. k_mp_refine      for every window: its candidate groups scored in float32,
+//                       the best re-scored exactly (compensated sums) where the
+//                       match is close, dist = sqrt(2 m (1 - rho)), plus the
+//                       constant-window rules.
+// After point updates (section 5 below) only the windows covering changed
+// samples, and those whose nearest neighbour was among them, are re-profiled.
 // The float64 variant (k_mp_diag_f64) is exact: one thread per diagonal, a
 // first pass takes the float64 maximum per window, a second pass the lowest
 // index attaining it.

@@ -723,6 +723,20 @@ __global__ void k_point_update(Acc* __restrict__ S, TX* __restrict__ T, const in
   }
 }
 
+// Self-test of the failure path: one warp waits, with the sketch kernel's
+// bounded wait, on an mbarrier phase that nothing completes (one arrival
+// expected, none made).  The wait gives up after ~1 s and flags a timeout in the
+// error word; no copy is in flight, so the block simply ends.
+__global__ void k_selftest_wait(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  __syncwarp();
+  mbar_wait_bounded(&bar, 0u, err);
+}
+
 }  // namespace
 
 tsk_status tsk_launch_colstats(tsk_ctx* ctx, const void* T, int t_dtype, const int64_t* d_off, const int32_t* d_len,
@@ -933,5 +947,11 @@ tsk_status tsk_launch_point_update(tsk_ctx* ctx, void* S, void* T, int t_dtype, 
                                                            d_delta, npts, d_cum, d_len, d, R, k, precision, stats);
   }
   TSK_LAUNCH_CHECK(ctx, "k_point_update");
+  return TSK_OK;
+}
+
+tsk_status tsk_launch_selftest_wait(tsk_ctx* ctx) {
+  k_selftest_wait<<<1, 32, 0, ctx->stream>>>(ctx->d_err);
+  TSK_LAUNCH_CHECK(ctx, "k_selftest_wait");
   return TSK_OK;
 }
