@@ -89,6 +89,12 @@ constexpr float kCloseKey = 0.02f;
 // correlation reaches this; below it float32 (~1e-6 in rho) gives the distance
 // to ~1e-4 relative (dist error ~ drho / (2 (1 - rho))), a tenth of the 1e-3 bar.
 constexpr float kExactRho = 0.99f;
+// A window whose nearest neighbour is within this of rho = 1 (its distance below
+// the bar's floor, where the bar is absolute), or a close match (1 - rho < 5e-3)
+// whose near-tie list overflowed, is re-scanned whole: every window within
+// kRescanTol (in rho) of the best float32 score is re-scored exactly.
+constexpr double kRescanGap = 1e-4;
+constexpr float kRescanTol = 4e-6f;
 
 struct WinArrays {
   double* mu;
@@ -850,10 +856,12 @@ struct GroupScan;
 
 template <>
 struct GroupScan<float> {
-  // best admissible window of group [p, p + 8) for window i (-1 if none)
-  static __device__ int best(const float* __restrict__ x, int i, const float* __restrict__ xp, int p, int m,
-                             double mu_i, const double* __restrict__ mup, const float* __restrict__ invp, int lp,
-                             int excl, bool ab, float* key = nullptr) {
+  // scores k[v] = rho(i, p + v) * ||x_i - mean|| of group [p, p + 8) for window
+  // i; -FLT_MAX for windows that are not admissible (outside the stream, inside
+  // the exclusion zone, constant)
+  static __device__ void scores(const float* __restrict__ x, int i, const float* __restrict__ xp, int p, int m,
+                                double mu_i, const double* __restrict__ mup, const float* __restrict__ invp, int lp,
+                                int excl, bool ab, float (&ks)[kVh]) {
     const float mih = static_cast<float>(mu_i), mil = static_cast<float>(mu_i - static_cast<double>(mih));
     const int pc = max(p, 0);
     const float ref = xp[pc];
@@ -888,19 +896,29 @@ struct GroupScan<float> {
         acc[v] = __fmaf_rn(at, (q >= 0 && q < np) ? __fsub_rn(xp[q], ref) : 0.f, acc[v]);
       }
     }
-    int bj = -1;
-    float bk = 0.f;
 #pragma unroll
     for (int v = 0; v < kVh; ++v) {
       const int j = p + v;
+      ks[v] = -FLT_MAX;
       if (j < 0 || j >= lp || (!ab && abs(i - j) < excl) || invp[j] == 0.f) continue;
       const float c = acc[v] - static_cast<float>(mup[j] - static_cast<double>(ref)) * sa;
-      const float k = c * invp[j];  // rho * norm_i: same scale for every candidate of window i
-      if (bj < 0 || k > bk) {
-        bj = j;
-        bk = k;
-      }
+      ks[v] = c * invp[j];  // rho * norm_i: same scale for every candidate of window i
     }
+  }
+  // best admissible window of the group (-1 if none), lowest index on ties
+  static __device__ int best(const float* __restrict__ x, int i, const float* __restrict__ xp, int p, int m,
+                             double mu_i, const double* __restrict__ mup, const float* __restrict__ invp, int lp,
+                             int excl, bool ab, float* key = nullptr) {
+    float ks[kVh];
+    scores(x, i, xp, p, m, mu_i, mup, invp, lp, excl, ab, ks);
+    int bj = -1;
+    float bk = 0.f;
+#pragma unroll
+    for (int v = 0; v < kVh; ++v)
+      if (ks[v] > -FLT_MAX && (bj < 0 || ks[v] > bk)) {
+        bj = p + v;
+        bk = ks[v];
+      }
     if (key) *key = bk;
     return bj;
   }
@@ -936,7 +954,9 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
                                                    const int64_t* __restrict__ woff, int n_streams, int64_t total, int m,
                                                    int excl, int exact64, WinArrays wa, TP* __restrict__ P,
                                                    int32_t* __restrict__ I, TP* __restrict__ P2,
-                                                   int32_t* __restrict__ I2, int keep_old = 0) {
+                                                   int32_t* __restrict__ I2, int keep_old = 0,
+                                                   int64_t* __restrict__ rescan = nullptr,
+                                                   unsigned int* __restrict__ rescan_n = nullptr) {
   const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= total) return;
   const int q = tsk_find_segment<int64_t>(xoff, n_streams, e);
@@ -1061,11 +1081,121 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
         }
       }
       if (j >= 0) dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, best_rho))));
+      // near ties decide the bar only for close matches (error ~ 1e-6 / (1 - rho))
+      if (rescan && j >= 0 && (1.0 - best_rho < kRescanGap || (wa.ncnt[wi] > kCand && 1.0 - best_rho < 5e-3)))
+        rescan[atomicAdd(rescan_n, 1u)] = e;
     }
   }
   if (jc >= 0 && (sqm < dist || (sqm == dist && jc < j))) { dist = sqm; j = jc; }
   Pout[eo] = static_cast<TP>(dist);
   Iout[eo] = j;
+}
+
+// ---------------------------------------------------------------------------
+// 4'. whole-row rescan of the windows the refinement listed: near-exact matches
+// (distance below the bar's floor) and windows whose near-tie list overflowed.
+// One warp per window: a first float32 sweep over every admissible partner
+// window (groups of 8, sliding dot products) finds the best score, a second
+// sweep re-scores exactly (compensated sums) every window within kRescanTol of
+// it.  The exact best, lowest index on ties, replaces the refinement's result;
+// the constant-window rule applies as there.  float32 series only.
+// ---------------------------------------------------------------------------
+template <bool AB>
+__global__ void __launch_bounds__(256) k_mp_rescan(const float* __restrict__ X, const float* __restrict__ X2, int split,
+                                                   const int64_t* __restrict__ xoff, const int32_t* __restrict__ len,
+                                                   const int64_t* __restrict__ woff, int n_streams, int m, int excl,
+                                                   WinArrays wa, float* __restrict__ P, int32_t* __restrict__ I,
+                                                   float* __restrict__ P2, int32_t* __restrict__ I2,
+                                                   const int64_t* __restrict__ rescan,
+                                                   const unsigned int* __restrict__ rescan_n) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
+  const long long n = static_cast<long long>(*rescan_n);
+  for (long long r = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nwarps) {
+    const int64_t e = rescan[r];
+    const int q = tsk_find_segment<int64_t>(xoff, n_streams, e);
+    float* Pout = P;
+    int32_t* Iout = I;
+    int64_t eo = e;
+    if (AB && q >= split) {
+      Pout = P2;
+      Iout = I2;
+      eo = e - xoff[split];
+    }
+    const int i = static_cast<int>(e - xoff[q]);
+    const int l = len[q] - m + 1;
+    const int p = AB ? (q < split ? q + split : q - split) : q;
+    const int lp = len[p] - m + 1;
+    const int64_t wb = woff[q], wbp = woff[p];
+    const float* x = AB ? stream_base(X, X2, xoff, split, q) : X + xoff[q];
+    const float* xp = AB ? stream_base(X, X2, xoff, split, p) : x;
+    const double mu_i = wa.mu[wb + i];
+    const double* mup = wa.mu + wbp;
+    const float* invp = wa.inv + wbp;
+    const int ex = AB ? 0 : excl;
+    // sweep 1: the best float32 score
+    float kmax = -FLT_MAX;
+    for (int g = lane * kVh; g < lp; g += 32 * kVh) {
+      float ks[kVh];
+      GroupScan<float>::scores(x, i, xp, g, m, mu_i, mup, invp, lp, ex, AB, ks);
+#pragma unroll
+      for (int v = 0; v < kVh; ++v) kmax = fmaxf(kmax, ks[v]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kmax = fmaxf(kmax, __shfl_xor_sync(TSK_FULL_MASK, kmax, o));
+    if (kmax == -FLT_MAX) continue;  // no non-constant partner: the refinement's result stands
+    const float thr = kmax - kRescanTol / fmaxf(wa.inv[wb + i], FLT_MIN);
+    // sweep 2: exact scores of every window within the tolerance
+    double brho = -2.0;
+    int bj = INT_MAX;
+    for (int g = lane * kVh; g < lp; g += 32 * kVh) {
+      float ks[kVh];
+      GroupScan<float>::scores(x, i, xp, g, m, mu_i, mup, invp, lp, ex, AB, ks);
+#pragma unroll
+      for (int v = 0; v < kVh; ++v) {
+        if (ks[v] < thr) continue;
+        const int j = g + v;
+        const double rho = tsk::window_rho(x, i, xp, j, m, mu_i, mup[j]);
+        if (rho > brho || (rho == brho && j < bj)) {
+          brho = rho;
+          bj = j;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double orho = __shfl_xor_sync(TSK_FULL_MASK, brho, o);
+      const int oj = __shfl_xor_sync(TSK_FULL_MASK, bj, o);
+      if (orho > brho || (orho == brho && oj < bj)) {
+        brho = orho;
+        bj = oj;
+      }
+    }
+    if (lane == 0 && bj != INT_MAX) {
+      double dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, brho))));
+      int j = bj;
+      // the constant-window rule (lowest admissible constant window at sqrt(m))
+      int jc = -1;
+      if (wa.constcnt[p] > 0) {
+        const int f = wa.nxt[wbp];
+        if (AB) {
+          if (f < lp) jc = f;
+        } else if (f <= i - excl) {
+          jc = f;
+        } else if (i + excl < l) {
+          const int gg = wa.nxt[wb + i + excl];
+          if (gg < l) jc = gg;
+        }
+      }
+      const double sqm = sqrt(static_cast<double>(m));
+      if (jc >= 0 && (sqm < dist || (sqm == dist && jc < j))) {
+        dist = sqm;
+        j = jc;
+      }
+      Pout[eo] = static_cast<float>(dist);
+      Iout[eo] = j;
+    }
+  }
 }
 
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel), and
@@ -1119,7 +1249,15 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
     wa.inv64 = cv.take<double>(W);
     wa.bidx = cv.take<int32_t>(W);
   }
+  // windows listed for a whole-row rescan (float32 series)
+  int64_t* rescan = nullptr;
+  unsigned int* rescan_n = nullptr;
+  if (!f64 && std::is_same<TX, float>::value) {
+    rescan = cv.take<int64_t>(W);
+    rescan_n = cv.take<unsigned int>(1);
+  }
   cudaStream_t st = ctx->stream;
+  if (rescan_n) TSK_CUDA_TRY(ctx, cudaMemsetAsync(rescan_n, 0, sizeof(unsigned int), st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.best, 0, sizeof(unsigned long long) * W, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.constcnt, 0, sizeof(int32_t) * n_streams, st));
   if (!f64) TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.ncnt, 0, sizeof(int32_t) * W, st));
@@ -1192,12 +1330,25 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
     else if (ab)
       k_mp_refine<TX, float, true><<<g, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.smask, plan.woff,
                                                       n_streams, total, m, 0, 0, wa, static_cast<float*>(P), I,
-                                                      static_cast<float*>(P2), I2);
+                                                      static_cast<float*>(P2), I2, 0, rescan, rescan_n);
     else
       k_mp_refine<TX, float, false><<<g, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.smask, plan.woff,
                                                        n_streams, total, m, excl, 0, wa, static_cast<float*>(P), I,
-                                                       nullptr, nullptr);
+                                                       nullptr, nullptr, 0, rescan, rescan_n);
     TSK_LAUNCH_CHECK(ctx, "k_mp_refine");
+    if constexpr (std::is_same<TX, float>::value) {
+      if (rescan) {
+        const unsigned gr = static_cast<unsigned>(ctx->sm_count * 8);
+        if (ab)
+          k_mp_rescan<true><<<gr, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.woff, n_streams, m, excl, wa,
+                                                static_cast<float*>(P), I, static_cast<float*>(P2), I2, rescan,
+                                                rescan_n);
+        else
+          k_mp_rescan<false><<<gr, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.woff, n_streams, m, excl,
+                                                 wa, static_cast<float*>(P), I, nullptr, nullptr, rescan, rescan_n);
+        TSK_LAUNCH_CHECK(ctx, "k_mp_rescan");
+      }
+    }
   }
   return TSK_OK;
 }
@@ -1472,6 +1623,8 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
   int32_t* rcount = cv.take<int32_t>(n_streams);                 // |R| per stream
   uint8_t* aflag = cv.take<uint8_t>(W);
   int32_t* rlist = cv.take<int32_t>(W);                          // R of stream q at woff[q]
+  int64_t* rescan = cv.take<int64_t>(W);                         // windows for a whole-row rescan
+  unsigned int* rescan_n = cv.take<unsigned int>(1);
   int4* d_runs = cv.take<int4>(runs.size());
   int4* d_tiles = cv.take<int4>(std::max<size_t>(tiles.size(), 1));
   cudaStream_t st = ctx->stream;
@@ -1479,6 +1632,7 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.constcnt, 0, sizeof(int32_t) * n_streams, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(rcount, 0, sizeof(int32_t) * n_streams, st));
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(rescan_n, 0, sizeof(unsigned int), st));
   // (copies from pageable memory return once staged, so the vectors may go out of scope)
   TSK_CUDA_TRY(ctx, cudaMemcpyAsync(d_runs, runs.data(), sizeof(int4) * runs.size(), cudaMemcpyHostToDevice, st));
   if (!tiles.empty())
@@ -1541,8 +1695,12 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
   }
   TSK_LAUNCH_CHECK(ctx, "k_upd_rowscan");
   k_mp_refine<float, float, false><<<gs, 256, 0, st>>>(X, X, n_streams, plan.xoff, plan.len, plan.smask, plan.woff,
-                                                       n_streams, total, m, excl, 0, wa, P, I, nullptr, nullptr, 1);
+                                                       n_streams, total, m, excl, 0, wa, P, I, nullptr, nullptr, 1,
+                                                       rescan, rescan_n);
   TSK_LAUNCH_CHECK(ctx, "k_mp_refine");
+  k_mp_rescan<false><<<static_cast<unsigned>(ctx->sm_count * 8), 256, 0, st>>>(
+      X, X, n_streams, plan.xoff, plan.len, plan.woff, n_streams, m, excl, wa, P, I, nullptr, nullptr, rescan, rescan_n);
+  TSK_LAUNCH_CHECK(ctx, "k_mp_rescan");
   return TSK_OK;
 }
 
@@ -1551,8 +1709,9 @@ size_t update_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams, size_t n_runs
   return tsk_carver::bytes_for(W, 8) * 2 + tsk_carver::bytes_for(W, 4) * 3 + tsk_carver::bytes_for(W, 8) +
          tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_streams, 4) + tsk_carver::bytes_for(W, 4) +
          tsk_carver::bytes_for(W * kCand, 8) + tsk_carver::bytes_for(1, 8) + tsk_carver::bytes_for(n_streams, 4) +
-         tsk_carver::bytes_for(W, 1) + tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_runs, 16) +
-         tsk_carver::bytes_for(n_tiles_max, 16) + 4096;
+         tsk_carver::bytes_for(W, 1) + tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(W, 8) +
+         tsk_carver::bytes_for(1, 4) + tsk_carver::bytes_for(n_runs, 16) + tsk_carver::bytes_for(n_tiles_max, 16) +
+         4096;
 }
 
 }  // namespace
@@ -1570,7 +1729,8 @@ size_t tsk_mp_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams) {
   if (plan.prec == TSK_MP_FP64)
     b += tsk_carver::bytes_for(W, 8) + tsk_carver::bytes_for(W, 4);
   else
-    b += tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(W * kCand, 8);
+    b += tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(W * kCand, 8) + tsk_carver::bytes_for(W, 8) +
+         tsk_carver::bytes_for(1, 4);
   return b + 4096;
 }
 
@@ -1722,7 +1882,8 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   const size_t o_nxt = off; off = align256(off + 4 * W);
   const size_t o_ncnt = off; off = align256(off + 4 * W);
   const size_t o_near = off; off = align256(off + 8 * kCand * W);
-  const size_t o_small = off; off = align256(off + 64);  // constcnt, counter, error word
+  const size_t o_rescan = off; off = align256(off + 8 * W);
+  const size_t o_small = off; off = align256(off + 64);  // constcnt, counter, error word, rescan count
   const size_t o_tiles = off; off = align256(off + sizeof(int4) * n_tiles);
   if (off > kStaticScratchBytes) return TSK_ERR_INVALID_ARG;
   char* sb = static_cast<char*>(base);
@@ -1792,8 +1953,15 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
     k_mp_diag<float, false><<<static_cast<unsigned>(grid), kWarps * 32, smem, stream>>>(a);
     if (!launched()) return TSK_ERR_CUDA;
   }
+  int64_t* rescan = reinterpret_cast<int64_t*>(sb + o_rescan);
+  unsigned int* rescan_n = reinterpret_cast<unsigned int*>(sb + o_small + 24);
   k_mp_refine<float, float, false><<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
-      X, X, 1, dh->xoff, dh->len, dh->smask, dh->woff, 1, n, m, excl, 0, wa, P, I, nullptr, nullptr);
+      X, X, 1, dh->xoff, dh->len, dh->smask, dh->woff, 1, n, m, excl, 0, wa, P, I, nullptr, nullptr, 0, rescan,
+      rescan_n);
+  if (!launched()) return TSK_ERR_CUDA;
+  k_mp_rescan<false><<<static_cast<unsigned>(sms * 8), 256, 0, stream>>>(X, X, 1, dh->xoff, dh->len, dh->woff, 1, m,
+                                                                         excl, wa, P, I, nullptr, nullptr, rescan,
+                                                                         rescan_n);
   if (!launched()) return TSK_ERR_CUDA;
   return TSK_OK;
 }
