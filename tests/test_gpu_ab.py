@@ -117,6 +117,23 @@ def test_close_matches_in_both_directions(tsk):
         _check_ab(B[q], A[q], m, P_b[ob[q]:ob[q] + l_b], I_b[ob[q]:ob[q] + l_b], rows=np.arange(0, l_b, 3))
 
 
+def test_near_exact_repeats_in_both_directions(tsk):
+    """Pure sines with noise 1e-4 in test and training: dozens of near-exact repeats per window
+    in the other stream, below float32 resolution; those rows are re-scanned exactly."""
+    rng = np.random.default_rng(59)
+    m = 64
+    A = [(np.sin(2 * np.pi * (np.arange(3000) + 5) / 64) + 1e-4 * rng.normal(size=3000)).astype(np.float32)]
+    B = [(np.sin(2 * np.pi * np.arange(3500) / 64) + 1e-4 * rng.normal(size=3500)).astype(np.float32)]
+    la, lb = [3000], [3500]
+    P_a, I_a, P_b, I_b = tsk.mp_abjoin(_pack(A, torch.float32), _pack(B, torch.float32), la, lb, m,
+                                       train_profile=True)
+    tsk.sync()
+    P_a, I_a, P_b, I_b = (t.cpu().numpy() for t in (P_a, I_a, P_b, I_b))
+    l_a, l_b = la[0] - m + 1, lb[0] - m + 1
+    _check_ab(A[0], B[0], m, P_a[:l_a], I_a[:l_a], rows=np.arange(0, l_a, 3))
+    _check_ab(B[0], A[0], m, P_b[:l_b], I_b[:l_b], rows=np.arange(0, l_b, 3))
+
+
 def test_sketched_and_exact_ab_discords_match_the_oracle(tsk):
     """Planted window in test only; bf16 sketch of train and test with one R, then Alg. 2 and Alg. 3."""
     d, n, m, k, K = 6, 2400, 40, 3, 3

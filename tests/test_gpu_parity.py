@@ -450,3 +450,20 @@ def test_close_matches_meet_the_tolerance(tsk):
     for x, (P, I) in zip(xs, out):
         l = len(x) - m + 1
         check_profile(x.astype(np.float64), m, excl, P[:l], I[:l], rows=np.arange(0, l, 3))
+
+
+def test_near_exact_repeats_meet_the_tolerance(tsk):
+    """Pure sines with noise 1e-3 and 1e-4 of the signal: every window has dozens of repeats
+    whose correlations differ by less than float32 resolves (~1e-6 in rho), and the distances
+    sit below the floor, where the bar is absolute.  Those rows are re-scanned exactly."""
+    rng = np.random.default_rng(67)
+    xs, ms = [], []
+    for n, period, noise in ((5000, 100, 1e-3), (4000, 64, 1e-4)):
+        t = np.arange(n)
+        xs.append((np.sin(2 * np.pi * t / period) + noise * rng.normal(size=n)).astype(np.float32))
+    m = 64
+    excl = int(math.ceil(m / 4))
+    out = _streams(tsk, xs, m, excl)
+    for x, (P, I) in zip(xs, out):
+        l = len(x) - m + 1
+        check_profile(x.astype(np.float64), m, excl, P[:l], I[:l], rows=np.arange(0, l, 3))

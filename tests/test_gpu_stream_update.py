@@ -130,6 +130,19 @@ def test_update_with_constant_windows(tsk):
     check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l], rows=_rows(l, changes, 0, m, stride=4))
 
 
+def test_update_of_near_exact_repeats(tsk):
+    """A sine with noise 1e-4: every window has dozens of near-exact repeats; a changed point
+    makes the windows over it the only ones far from them, and the rest keep exact choices."""
+    rng = np.random.default_rng(96)
+    m, excl = 64, 16
+    n = 12000
+    x = np.sin(2 * np.pi * np.arange(n) / 64) + 1e-4 * rng.normal(size=n)
+    changes = {(0, 5000): 0.3, (0, 9100): -0.01}
+    new, P, I, _, _ = _run(tsk, [x], m, excl, changes)
+    l = n - m + 1
+    check_profile(new[0].astype(np.float64), m, excl, P[:l], I[:l], rows=_rows(l, changes, 0, m, stride=6))
+
+
 def test_update_rejects_points_out_of_range(tsk):
     X = torch.zeros(1000, device="cuda")
     P, I = tsk.mp_selfjoin(torch.randn(1000, device="cuda"), [1000], 20)

@@ -44,8 +44,12 @@ def test_static_entry_point_matches_mp_selfjoin_on_two_calls(libs):
     tsk, lib = libs
     m, excl = 100, 25
     floor = d_floor(m)
-    for seed, n in ((300, 5000), (301, 2300)):
-        x = np.cumsum(np.random.default_rng(seed).normal(size=n)).astype(np.float32)
+    for seed, n in ((300, 5000), (301, 2300), (303, 4000)):
+        rng = np.random.default_rng(seed)
+        if seed == 303:  # a sine with noise 1e-4: near-exact repeats below float32 resolution
+            x = (np.sin(2 * np.pi * np.arange(n) / 64) + 1e-4 * rng.normal(size=n)).astype(np.float32)
+        else:
+            x = np.cumsum(rng.normal(size=n)).astype(np.float32)
         X = torch.from_numpy(x).cuda()
         P, I = _static_call(lib, X, n, m, excl)
         P_ref, I_ref = tsk.mp_selfjoin(X, [n], m, excl)
