@@ -402,6 +402,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
           }
         }
       }
+      __syncthreads();  // qlist is rewritten by the next batch's selection
     }
     __syncthreads();  // shared buffers are reused by the next item
   }

@@ -123,6 +123,25 @@ def test_ragged_batch_every_score(tsk, kind):
         _check_dims(T, R, queries[s], m, excl, {key: v[s] for key, v in got.items()})
 
 
+@pytest.mark.parametrize("m", [40, 512, 600])
+def test_more_discords_than_a_batch_holds(tsk, m):
+    """20 discords per series: the scan stages at most 16 per batch (fewer for long windows: 14 at
+    m = 512 and 600), so a second batch follows the first on every chunk.  A stream with a large
+    offset and a small spread; float32 and float64."""
+    rng = np.random.default_rng(24 + m)
+    d, k, n = 4, 2, 4200
+    excl = synth.default_excl(m)
+    T = np.cumsum(rng.normal(size=(d, n)), axis=1)
+    T[2] = 1.0e4 + 1e-2 * T[2]
+    R = synth.gaussian_R(d, k, 6)
+    l = n - m + 1
+    queries = [(int(i), int(rng.integers(0, k))) for i in rng.integers(0, l, 20)]
+    for dtype in (torch.float32, torch.float64):
+        Ts = T.astype(np.float32) if dtype == torch.float32 else T
+        _, _, got = _run(tsk, [Ts], R, [queries], m, excl, dtype)
+        _check_dims(Ts, R, queries, m, excl, {key: v[0] for key, v in got.items()})
+
+
 def test_constant_windows_empty_group_and_no_neighbour(tsk):
     n, m, excl = 1500, 32, 8
     rng = np.random.default_rng(7)
