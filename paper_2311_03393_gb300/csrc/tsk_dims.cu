@@ -23,11 +23,11 @@
 //                   the loads are free of bank conflicts).  The largest key
 //                   rho - 1 and lowest window index merge per (series,
 //                   discord, stream) in a packed 64-bit word with atomicMax.
-//   3. k_dd_select  one CTA per (series, discord): warps take the streams of the
-//                   group in turn, a whole warp re-evaluates each chosen window
-//                   exactly (compensated sums), then the strict running maximum
-//                   over ascending j.
-//   4. k_dd_gather  (optional) copies stream j* of every discord into a
+//   3. k_dd_exact   one warp per (series, discord, stream): the chosen window
+//                   re-evaluated exactly (compensated sums).
+//   4. k_dd_select  one CTA per (series, discord): the strict running maximum
+//                   over ascending j, as a reduction.
+//   5. k_dd_gather  (optional) copies stream j* of every discord into a
 //                   contiguous buffer for a self-join refinement profile.
 #include "tsk_internal.cuh"
 #include "tsk_ff.cuh"
@@ -65,6 +65,8 @@ struct DimArgs {
   unsigned long long* best;    // n_series x K x d
   float* Q;                    // n_series x K x d x m4: centred queries
   float4* qinfo;               // n_series x K x d: {1/||q||, sum(q), active, constant}
+  double* sc;                  // n_series x K x d: exact score of each stream's chosen window
+  int32_t* nn;                 // n_series x K x d: that window
   int n_series, d, k, m, m4, excl, K;
 };
 
@@ -473,63 +475,107 @@ __device__ double warp_window_dist(const TX* xq, int i, const TX* x, int t, int 
   return sqrt(fmax(0.0, 2.0 * m * (1.0 - rho)));
 }
 
-// One CTA (8 warps) per (series, discord): warps take the streams j of the
-// group in turn and re-evaluate each chosen window exactly; then Alg. 3's
-// strict running maximum over ascending j (the larger score, then the lower j).
+// One warp per (series, discord, stream): the stream's chosen window
+// re-evaluated exactly.  NaN: the stream is not in the discord's group; +inf:
+// no admissible neighbour.
 template <typename TX>
-__global__ void __launch_bounds__(256) k_dd_select(const TX* __restrict__ Tq, const TX* __restrict__ T, DimArgs a,
-                                                   int32_t* __restrict__ dim, double* __restrict__ dim_score,
-                                                   int32_t* __restrict__ dim_nn, double* __restrict__ dim_scores) {
-  const int64_t sr = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kW = 8;
+__global__ void __launch_bounds__(256) k_dd_exact(const TX* __restrict__ Tq, const TX* __restrict__ T, DimArgs a,
+                                                  double* __restrict__ sc_out, int32_t* __restrict__ nn_out,
+                                                  double* __restrict__ dim_scores) {
+  const int64_t wid = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= static_cast<int64_t>(a.n_series) * a.K * a.d) return;
+  const int j = static_cast<int>(wid % a.d);
+  const int64_t sr = wid / a.d;
   const int s = static_cast<int>(sr / a.K);
   const int n = a.len[s];
   const int l = n - a.m + 1;
   const int i_star = a.idx[sr];
   const int g_star = a.grp[sr];
   const bool valid = i_star >= 0 && i_star < l && g_star >= 0 && g_star < a.k;
-  double bs = 0.0;  // strict running maximum from 0 over this warp's j (ascending)
-  int bj = -1, bnn = -1;
-  int first = a.d;  // lowest j of the group seen by this warp
-  double first_s = 0.0;
-  int first_nn = -1;
-  for (int j = warp; j < a.d; j += kW) {
-    double sc = NAN;
-    int nn = -1;
-    if (valid && a.R[static_cast<int64_t>(j) * a.k + g_star] != 0.f) {
-      const unsigned long long p = a.best[sr * a.d + j];
-      if (p == 0ull) {
-        sc = INFINITY;  // no admissible neighbour
-      } else {
-        nn = tsk_unpack_idx(p);
-        const TX* xq = Tq + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n;
-        const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * a.len_t[s];
-        sc = warp_window_dist(xq, i_star, x, nn, a.m);
-      }
-      if (j < first) { first = j; first_s = sc; first_nn = nn; }
-      if (sc > bs) { bs = sc; bj = j; bnn = nn; }
+  double sc = NAN;
+  int nn = -1;
+  if (valid && a.R[static_cast<int64_t>(j) * a.k + g_star] != 0.f) {
+    const unsigned long long p = a.best[wid];
+    if (p == 0ull) {
+      sc = INFINITY;
+    } else {
+      nn = tsk_unpack_idx(p);
+      const TX* xq = Tq + a.cum[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n;
+      const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * a.len_t[s];
+      sc = warp_window_dist(xq, i_star, x, nn, a.m);
     }
-    if (dim_scores && lane == 0) dim_scores[sr * a.d + j] = sc;
   }
-  __shared__ double sbs[kW], sfs[kW];
-  __shared__ int sbj[kW], sbn[kW], sfj[kW], sfn[kW];
   if (lane == 0) {
-    sbs[warp] = bs; sbj[warp] = bj; sbn[warp] = bnn;
-    sfs[warp] = first_s; sfj[warp] = first; sfn[warp] = first_nn;
+    sc_out[wid] = sc;
+    nn_out[wid] = nn;
+    if (dim_scores) dim_scores[wid] = sc;
+  }
+}
+
+// One CTA per (series, discord): Alg. 3's strict running maximum from 0 over
+// ascending j, i.e. the largest score above 0 (the lowest j among equal ones),
+// else the group's first stream; -1 for an empty group or an invalid discord.
+__global__ void __launch_bounds__(256) k_dd_select(DimArgs a, const double* __restrict__ sc, const int32_t* __restrict__ nn,
+                                                   int32_t* __restrict__ dim, double* __restrict__ dim_score,
+                                                   int32_t* __restrict__ dim_nn) {
+  const int64_t sr = blockIdx.x;
+  const double* v = sc + sr * a.d;
+  double bs = 0.0;
+  int bj = -1, first = a.d;
+  for (int j = threadIdx.x; j < a.d; j += blockDim.x) {  // ascending j per thread: ties keep the lower j
+    const double x = v[j];
+    if (isnan(x)) continue;  // not in the group
+    first = min(first, j);
+    if (x > bs) {
+      bs = x;
+      bj = j;
+    }
+  }
+  auto better = [](double s1, int j1, double s2, int j2) {  // (s2, j2) replaces (s1, j1)
+    return j2 >= 0 && (j1 < 0 || s2 > s1 || (s2 == s1 && j2 < j1));
+  };
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_xor_sync(TSK_FULL_MASK, bs, o);
+    const int j2 = __shfl_xor_sync(TSK_FULL_MASK, bj, o);
+    const int f2 = __shfl_xor_sync(TSK_FULL_MASK, first, o);
+    if (better(bs, bj, s2, j2)) {
+      bs = s2;
+      bj = j2;
+    }
+    first = min(first, f2);
+  }
+  __shared__ double wbs[8];
+  __shared__ int wbj[8], wf[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    wbs[warp] = bs;
+    wbj[warp] = bj;
+    wf[warp] = first;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b = 0.0;
-    int j0 = -1, n0 = -1, f = a.d, fn = -1;
-    double fs = 0.0;
-    for (int w = 0; w < kW; ++w) {
-      if (sbj[w] >= 0 && (j0 < 0 || sbs[w] > b || (sbs[w] == b && sbj[w] < j0))) { b = sbs[w]; j0 = sbj[w]; n0 = sbn[w]; }
-      if (sfj[w] < f) { f = sfj[w]; fs = sfs[w]; fn = sfn[w]; }
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+      if (better(bs, bj, wbs[w], wbj[w])) {
+        bs = wbs[w];
+        bj = wbj[w];
+      }
+      first = min(first, wf[w]);
     }
-    if (j0 >= 0) { dim[sr] = j0; dim_score[sr] = b; dim_nn[sr] = n0; }
-    else if (f < a.d) { dim[sr] = f; dim_score[sr] = fs; dim_nn[sr] = fn; }
-    else { dim[sr] = -1; dim_score[sr] = NAN; dim_nn[sr] = -1; }
+    if (bj >= 0) {
+      dim[sr] = bj;
+      dim_score[sr] = bs;
+      dim_nn[sr] = nn[sr * a.d + bj];
+    } else if (first < a.d) {
+      dim[sr] = first;
+      dim_score[sr] = v[first];
+      dim_nn[sr] = nn[sr * a.d + first];
+    } else {
+      dim[sr] = -1;
+      dim_score[sr] = NAN;
+      dim_nn[sr] = -1;
+    }
   }
 }
 
@@ -585,8 +631,10 @@ tsk_status run_dims(tsk_ctx* ctx, const TX* T, const TX* Tt, const DimArgs& a, i
     k_dd_scan<TX><<<static_cast<unsigned>(grid), kScanThreads, smem, st>>>(Tt, a, total_items);
     TSK_LAUNCH_CHECK(ctx, "k_dd_scan");
   }
-  const int64_t warps = static_cast<int64_t>(a.n_series) * a.K;
-  k_dd_select<TX><<<static_cast<unsigned>(warps), 256, 0, st>>>(T, Tt, a, dim, dim_score, dim_nn, dim_scores);
+  k_dd_exact<TX><<<static_cast<unsigned>((triples * 32 + 255) / 256), 256, 0, st>>>(T, Tt, a, a.sc, a.nn, dim_scores);
+  TSK_LAUNCH_CHECK(ctx, "k_dd_exact");
+  const int64_t discords = static_cast<int64_t>(a.n_series) * a.K;
+  k_dd_select<<<static_cast<unsigned>(discords), 256, 0, st>>>(a, a.sc, a.nn, dim, dim_score, dim_nn);
   TSK_LAUNCH_CHECK(ctx, "k_dd_select");
   if (T_sel && total_samples > 0) {
     const int64_t total = total_samples * a.K;
@@ -630,6 +678,8 @@ tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, const void* T_train, int
   a.best = cv.take<unsigned long long>(triples);
   a.Q = cv.take<float>(triples * a.m4);
   a.qinfo = cv.take<float4>(triples);
+  a.sc = cv.take<double>(triples);
+  a.nn = cv.take<int32_t>(triples);
   a.n_series = n_series;
   a.d = d;
   a.k = k;
@@ -648,5 +698,5 @@ tsk_status tsk_launch_dims(tsk_ctx* ctx, const void* T, const void* T_train, int
 size_t tsk_dims_ws_bytes(int32_t n_series, int32_t K, int32_t d, int32_t m) {
   const size_t triples = static_cast<size_t>(n_series) * K * d;
   return tsk_carver::bytes_for(triples, 8) + tsk_carver::bytes_for(triples * ((m + 3) & ~3), 4) +
-         tsk_carver::bytes_for(triples, 16);
+         tsk_carver::bytes_for(triples, 16) + tsk_carver::bytes_for(triples, 8) + tsk_carver::bytes_for(triples, 4);
 }
