@@ -17,12 +17,15 @@
 //                   shared memory shifted by its first sample; window means and
 //                   norms come from float-float prefix sums (no float64 on the
 //                   hot path: the FP64 pipe runs at 1/64 of FP32); each thread
-//                   forms 8 consecutive sliding dot products with two centred
-//                   queries at a time in paired float32 FMAs (64 FMAs in 32
+//                   forms 8 consecutive sliding dot products with four centred
+//                   queries at a time in paired float32 FMAs (128 FMAs in 64
 //                   issue slots per vector load of samples; swizzled staging so
-//                   the loads are free of bank conflicts).  The largest key
-//                   rho - 1 and lowest window index merge per (series,
-//                   discord, stream) in a packed 64-bit word with atomicMax.
+//                   the loads are free of bank conflicts).  The active
+//                   discords of an item are found once (one per thread, then
+//                   compacted).  Each thread keeps its best window per
+//                   discord; the largest key rho - 1 and lowest window index
+//                   merge per (series, discord, stream) in a packed 64-bit word
+//                   with atomicMax.
 //   3. k_dd_exact   one warp per (series, discord, stream): the chosen window
 //                   re-evaluated exactly (compensated sums).
 //   4. k_dd_select  one CTA per (series, discord): the strict running maximum
@@ -34,6 +37,7 @@
 #include "tsk_rho.cuh"
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <type_traits>
 
@@ -42,14 +46,14 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kWinPerThread = 8;                      // consecutive windows per thread
 constexpr int kTW = kScanThreads * kWinPerThread;     // 2048 windows per scan item
-constexpr int kQB = 16;                               // discords staged per batch (at most; even)
+constexpr int kQB = 16;                               // discords staged per batch (at most)
 constexpr int kQBudget = 8192;                        // floats of staged queries (32 KB)
 
-// discords staged per batch for subsequence length m (even, 2..kQB)
+// discords staged per batch for subsequence length m (a multiple of 4 up to kQB, else 2)
 __host__ __device__ inline int query_batch(int m) {
   const int m4 = (m + 3) & ~3;
   const int q = kQBudget / m4;
-  return q >= kQB ? kQB : (q < 2 ? 2 : (q & ~1));
+  return q >= kQB ? kQB : (q < 4 ? 2 : (q & ~3));
 }
 constexpr double kConstRelVar = 1e-12;
 
@@ -147,10 +151,12 @@ __global__ void __launch_bounds__(256) k_dd_query(const TX* __restrict__ T, DimA
 // Sliding dot products of the centred queries with the 8 consecutive windows
 // starting at staged sample w0.  One query (qs contiguous): 32 FMAs per 16-byte
 // load of samples.  Two queries (qs interleaved, qs[2k + q]): paired FFMA2 with
-// (sample, sample) x (q0_k, q1_k), 64 FMAs in 32 issue slots per load.
+// (sample, sample) x (q0_k, q1_k), 64 FMAs in 32 issue slots per load.  Four
+// queries (qs[4k + q]): each (sample, sample) pair feeds two FFMA2s, 128 FMAs
+// per load of samples.
 template <int NQ>
 __device__ __forceinline__ void dot_windows(const float* __restrict__ xs, const float* __restrict__ qs, int m4,
-                                            int w0, float (&acc)[2][kWinPerThread]) {
+                                            int w0, float (&acc)[4][kWinPerThread]) {
   float4 A = *reinterpret_cast<const float4*>(xs + xs_phys(w0));
   float4 B = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + 4));
   if constexpr (NQ == 1) {
@@ -169,6 +175,34 @@ __device__ __forceinline__ void dot_windows(const float* __restrict__ xs, const 
       }
       A = B;
       B = C;
+    }
+  } else if constexpr (NQ == 4) {
+    float2 acc2[kWinPerThread][2];
+#pragma unroll
+    for (int u = 0; u < kWinPerThread; ++u) acc2[u][0] = acc2[u][1] = make_float2(0.f, 0.f);
+    for (int kk = 0; kk < m4; kk += 4) {
+      const float4 C = *reinterpret_cast<const float4*>(xs + xs_phys(w0 + kk + 8));
+      const float v[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4 q = *reinterpret_cast<const float4*>(qs + 4 * (kk + k));  // (q0, q1, q2, q3) at tap kk + k
+        const float2 q01 = make_float2(q.x, q.y), q23 = make_float2(q.z, q.w);
+#pragma unroll
+        for (int u = 0; u < kWinPerThread; ++u) {
+          const float2 vv = make_float2(v[u + k], v[u + k]);
+          acc2[u][0] = __ffma2_rn(vv, q01, acc2[u][0]);
+          acc2[u][1] = __ffma2_rn(vv, q23, acc2[u][1]);
+        }
+      }
+      A = B;
+      B = C;
+    }
+#pragma unroll
+    for (int u = 0; u < kWinPerThread; ++u) {
+      acc[0][u] = acc2[u][0].x;
+      acc[1][u] = acc2[u][0].y;
+      acc[2][u] = acc2[u][1].x;
+      acc[3][u] = acc2[u][1].y;
     }
   } else {
     float2 acc2[kWinPerThread];
@@ -207,7 +241,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
   float* xs = reinterpret_cast<float*>(smem_raw);              // [xs_phys(ns_max)]
   const int xs_words = ns_max + 8;
   const int qb = query_batch(m);
-  float* qbuf = xs + xs_words;                                 // [qb * m4] staged queries (pairs interleaved)
+  float* qbuf = xs + xs_words;                                 // [qb * m4] staged queries (fours, pairs, taps interleaved)
   float* w_inv = qbuf + qb * m4;                               // [kTW] 1/||window - mean|| (0: constant)
   float* w_mean = w_inv + kTW;                                 // [kTW] window mean of the shifted samples
   float* p1h = w_mean + kTW;                                   // [kTW + m] prefix of shifted samples (float-float)
@@ -215,8 +249,11 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
   float* p2h = p1l + (kTW + m);                                // [kTW + m] prefix of their squares
   float* p2l = p2h + (kTW + m);
   __shared__ float segs[4][kScanThreads];
-  __shared__ int qlist[kQB];
-  const int tid = threadIdx.x;
+  __shared__ int act[kScanThreads];  // active discords r of the item (ascending), up to 256 at a time
+  __shared__ int wcnt[kScanThreads / 32];
+  __shared__ float4 qinf[kQB];
+  __shared__ int qstar[kQB];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     const int s = tsk_find_segment<int64_t>(a.item_prefix, a.n_series, item);
@@ -228,183 +265,239 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
     const int j = static_cast<int>(rem / chunks);
     const int t0 = c * kTW;
     const int nw = min(kTW, l - t0);
-    // any discord of this series whose group holds stream j and whose exclusion zone leaves a window here
-    bool any = false;
-    for (int r = 0; r < a.K; ++r) {
-      const int64_t qi = (static_cast<int64_t>(s) * a.K + r) * a.d + j;
-      if (a.qinfo[qi].z != 0.f) {
-        const int i_star = a.idx[static_cast<int64_t>(s) * a.K + r];
-        if (!(t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl)) any = true;
-      }
+    const int w0 = tid * kWinPerThread;  // this thread's 8 windows
+    if (item + gridDim.x < total_items) {  // the next item's samples into L2 while this one runs
+      const int64_t nx = item + gridDim.x;
+      const int s2 = tsk_find_segment<int64_t>(a.item_prefix, a.n_series, nx);
+      const int n2 = a.len_t[s2];
+      const int ch2 = (n2 - m + 1 + kTW - 1) / kTW;
+      const int64_t rem2 = nx - a.item_prefix[s2];
+      const int t02 = static_cast<int>(rem2 % ch2) * kTW;
+      const int nw2 = min(kTW, n2 - m + 1 - t02);
+      const char* px = reinterpret_cast<const char*>(T + a.cum_t[s2] * static_cast<int64_t>(a.d) +
+                                                     static_cast<int64_t>(rem2 / ch2) * n2 + t02);
+      const int bytes = (nw2 + m - 1) * static_cast<int>(sizeof(TX));
+      for (int o = tid * 128; o < bytes; o += kScanThreads * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(px + o));
     }
-    if (!any) continue;
-    const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n + t0;
-
-    // ---- stage the chunk shifted by its first sample; float-float prefix sums ----
-    const TX x_ref = x[0];
-    const int ns = nw + m - 1;
-    for (int p = tid; p < ns_max; p += kScanThreads) xs[xs_phys(p)] = (p < ns) ? ff_shift(x[p], x_ref).h : 0.f;
-    const int seg = (ns + kScanThreads - 1) / kScanThreads;
-    const int lo = tid * seg, hi = min(ns, lo + seg);
-    FF a1{0.f, 0.f}, a2{0.f, 0.f};
-    for (int p = lo; p < hi; ++p) {
-      const FF y = ff_shift(x[p], x_ref);
-      a1 = ff_add(a1, y);
-      a2 = ff_add(a2, ff_sqr(y));
-      p1h[p + 1] = a1.h; p1l[p + 1] = a1.l;
-      p2h[p + 1] = a2.h; p2l[p + 1] = a2.l;
-    }
-    segs[0][tid] = a1.h; segs[1][tid] = a1.l; segs[2][tid] = a2.h; segs[3][tid] = a2.l;
-    __syncthreads();
-    if (tid < 32) {  // exclusive scan of the 256 segment totals (float-float) by one warp
-      FF c1{0.f, 0.f}, c2{0.f, 0.f};
-      for (int q = 0; q < kScanThreads / 32; ++q) {
-        const int u = q * 32 + tid;
-        FF i1{segs[0][u], segs[1][u]}, i2{segs[2][u], segs[3][u]};
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const FF t1 = ff_shfl_up(i1, o), t2 = ff_shfl_up(i2, o);
-          if (tid >= o) { i1 = ff_add(i1, t1); i2 = ff_add(i2, t2); }
-        }
-        FF e1 = ff_shfl_up(i1, 1), e2 = ff_shfl_up(i2, 1);  // exclusive within the warp
-        if (tid == 0) { e1 = FF{0.f, 0.f}; e2 = FF{0.f, 0.f}; }
-        e1 = ff_add(c1, e1);
-        e2 = ff_add(c2, e2);
-        c1 = ff_add(c1, ff_shfl(i1, 31));
-        c2 = ff_add(c2, ff_shfl(i2, 31));
-        segs[0][u] = e1.h; segs[1][u] = e1.l; segs[2][u] = e2.h; segs[3][u] = e2.l;
-      }
-    }
-    __syncthreads();
-    {
-      const FF o1{segs[0][tid], segs[1][tid]}, o2{segs[2][tid], segs[3][tid]};
-      if (tid == 0) { p1h[0] = 0.f; p1l[0] = 0.f; p2h[0] = 0.f; p2l[0] = 0.f; }
-      for (int p = lo; p < hi; ++p) {
-        const FF v1 = ff_add(o1, FF{p1h[p + 1], p1l[p + 1]});
-        const FF v2 = ff_add(o2, FF{p2h[p + 1], p2l[p + 1]});
-        p1h[p + 1] = v1.h; p1l[p + 1] = v1.l;
-        p2h[p + 1] = v2.h; p2l[p + 1] = v2.l;
-      }
-    }
-    __syncthreads();
-    // ---- window statistics: D = m * sum(y^2) - sum(y)^2 = m^2 var ----
-    // A window whose D is within the prefix sums' rounding of the constant
-    // threshold is decided from its samples: all equal (constant), else the
-    // float64 two-pass variance.
-    const float fm = static_cast<float>(m);
-    const float m_ref = fm * static_cast<float>(x_ref);
-    const float sqrt_m = sqrtf(fm);
-    for (int w = tid; w < nw; w += kScanThreads) {
-      const FF s1 = ff_add(FF{p1h[w + m], p1l[w + m]}, ff_neg(FF{p1h[w], p1l[w]}));
-      const FF s2 = ff_add(FF{p2h[w + m], p2l[w + m]}, ff_neg(FF{p2h[w], p2l[w]}));
-      const FF D = ff_add(ff_mul(s2, fm), ff_neg(ff_sqr(s1)));
-      const float Df = D.h + D.l;
-      const float mmu = m_ref + s1.h;                         // m * window mean
-      const float thr = static_cast<float>(kConstRelVar) * fmaxf(fm * fm, mmu * mmu);
-      const float slack = 0x1p-30f * fm * (p2h[w + m] + p2h[w]);
-      float inv;
-      if (Df > thr + slack) {
-        inv = sqrt_m * rsqrtf(Df);
-      } else {
-        bool equal = true;
-        for (int t = 1; t < m && equal; ++t) equal = (x[w + t] == x[w]);
-        if (equal) {
-          inv = 0.f;
-        } else {
-          double mu = 0.0;
-          for (int t = 0; t < m; ++t) mu += static_cast<double>(x[w + t]);
-          mu /= m;
-          double v = 0.0;
-          for (int t = 0; t < m; ++t) {
-            const double dv = static_cast<double>(x[w + t]) - mu;
-            v += dv * dv;
-          }
-          inv = (v / m <= kConstRelVar * fmax(1.0, mu * mu)) ? 0.f : static_cast<float>(1.0 / sqrt(v));
-        }
-      }
-      w_inv[w] = inv;
-      w_mean[w] = s1.h / fm;
-    }
-    __syncthreads();
-
-    // this thread's 8 windows: statistics once per item (vector loads)
-    const int w0 = tid * kWinPerThread;
-    float winv[kWinPerThread], wmean[kWinPerThread];
-    {
-      const float4 i0 = *reinterpret_cast<const float4*>(w_inv + w0);
-      const float4 i1 = *reinterpret_cast<const float4*>(w_inv + w0 + 4);
-      const float4 m0 = *reinterpret_cast<const float4*>(w_mean + w0);
-      const float4 m1 = *reinterpret_cast<const float4*>(w_mean + w0 + 4);
-      winv[0] = i0.x; winv[1] = i0.y; winv[2] = i0.z; winv[3] = i0.w;
-      winv[4] = i1.x; winv[5] = i1.y; winv[6] = i1.z; winv[7] = i1.w;
-      wmean[0] = m0.x; wmean[1] = m0.y; wmean[2] = m0.z; wmean[3] = m0.w;
-      wmean[4] = m1.x; wmean[5] = m1.y; wmean[6] = m1.z; wmean[7] = m1.w;
-    }
-
-    // ---- the discords whose group holds this stream: up to kQB of them staged at
-    // once (two per slot, interleaved for paired FMAs); then every warp runs its
-    // 256 windows through them on its own and merges with one atomic per query
-    int r = 0;
-    for (;;) {
-      // next batch of active discords (the same list on every thread)
-      int nb = 0;
-      for (; r < a.K && nb < qb; ++r) {
+    bool staged = false;
+    for (int r0 = 0; r0 < a.K; r0 += kScanThreads) {
+      // discords r0 .. r0 + 255 whose group holds stream j and whose exclusion zone
+      // leaves a window in this chunk, compacted in ascending r (one per thread)
+      const int r = r0 + tid;
+      bool on = false;
+      if (r < a.K) {
         const int64_t sr = static_cast<int64_t>(s) * a.K + r;
-        if (a.qinfo[sr * a.d + j].z == 0.f) continue;
-        const int i_star = a.idx[sr];
-        if (t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl) continue;
-        if (tid == 0) qlist[nb] = r;
-        ++nb;
-      }
-      if (nb == 0) break;
-      __syncthreads();  // qlist written; the previous batch's queries no longer read
-      for (int b = 0; b < nb; b += 2) {
-        float* qs = qbuf + b * m4;  // slot b / 2: 2 * m4 floats
-        const float* qa = a.Q + ((static_cast<int64_t>(s) * a.K + qlist[b]) * a.d + j) * m4;
-        if (b + 1 < nb) {
-          const float* qb = a.Q + ((static_cast<int64_t>(s) * a.K + qlist[b + 1]) * a.d + j) * m4;
-          for (int t = tid; t < m4; t += kScanThreads) *reinterpret_cast<float2*>(qs + 2 * t) = make_float2(qa[t], qb[t]);
-        } else {
-          for (int t = tid; t < m4; t += kScanThreads) qs[t] = qa[t];
+        if (a.qinfo[sr * a.d + j].z != 0.f) {
+          const int i_star = a.idx[sr];
+          on = !(t0 > i_star - a.excl && t0 + nw - 1 < i_star + a.excl);
         }
       }
+      const unsigned bal = __ballot_sync(TSK_FULL_MASK, on);
+      if (lane == 0) wcnt[warp] = __popc(bal);
       __syncthreads();
-      for (int b = 0; b < nb; b += 2) {
-        const int nq = (b + 1 < nb) ? 2 : 1;
-        float acc[2][kWinPerThread];
-        if (nq == 2)
-          dot_windows<2>(xs, qbuf + b * m4, m4, w0, acc);
-        else
-          dot_windows<1>(xs, qbuf + b * m4, m4, w0, acc);
+      int base = 0, total = 0;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          if (q < nq) {
-            const int64_t sr = static_cast<int64_t>(s) * a.K + qlist[b + q];
-            const float4 qi = a.qinfo[sr * a.d + j];
-            const int i_star = a.idx[sr];
-            unsigned long long best = 0ull;
+      for (int u = 0; u < kScanThreads / 32; ++u) {
+        base += (u < warp) ? wcnt[u] : 0;
+        total += wcnt[u];
+      }
+      if (on) act[base + __popc(bal & ((1u << lane) - 1u))] = r;
+      __syncthreads();  // act written; wcnt read (the next chunk rewrites it)
+      if (total == 0) continue;
+      if (!staged) {
+        staged = true;
+        const TX* x = T + a.cum_t[s] * static_cast<int64_t>(a.d) + static_cast<int64_t>(j) * n + t0;
+
+        // ---- stage the chunk shifted by its first sample; float-float prefix sums ----
+        const TX x_ref = x[0];
+        const int ns = nw + m - 1;
+        // loads issued four at a time before their stores (memory-level parallelism)
+        for (int p0 = tid; p0 < ns_max; p0 += 4 * kScanThreads) {
+          TX v[4];
 #pragma unroll
-            for (int u = 0; u < kWinPerThread; ++u) {
-              const int w = w0 + u;
-              const int t = t0 + w;
-              if (w >= nw || (t > i_star - a.excl && t < i_star + a.excl)) continue;
-              const float inv_t = winv[u];
-              float key;
-              if (qi.w != 0.f) key = (inv_t == 0.f) ? 0.0f : -0.5f;  // rho 1 (dist 0) to a constant window, else 1/2
-              else if (inv_t == 0.f) key = -0.5f;                     // rho 1/2: 2m(1 - 1/2) = m
-              else {
-                const float cov = __fmaf_rn(-wmean[u], qi.y, acc[q][u]);
-                key = fminf(0.0f, fmaxf(-2.0f, __fmaf_rn(cov * qi.x, inv_t, -1.0f)));  // rho - 1
-              }
-              best = umax64(best, tsk_pack(key, t));
-            }
+          for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u * kScanThreads;
+            v[u] = (p < ns) ? x[p] : x_ref;
+          }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
-            if ((tid & 31) == 0 && best) atomicMax(&a.best[sr * a.d + j], best);
+          for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u * kScanThreads;
+            if (p < ns_max) xs[xs_phys(p)] = (p < ns) ? ff_shift(v[u], x_ref).h : 0.f;
           }
         }
+        const int seg = (ns + kScanThreads - 1) / kScanThreads;
+        const int lo = tid * seg, hi = min(ns, lo + seg);
+        FF a1{0.f, 0.f}, a2{0.f, 0.f};
+        for (int p = lo; p < hi; ++p) {
+          const FF y = ff_shift(x[p], x_ref);
+          a1 = ff_add(a1, y);
+          a2 = ff_add(a2, ff_sqr(y));
+          p1h[p + 1] = a1.h; p1l[p + 1] = a1.l;
+          p2h[p + 1] = a2.h; p2l[p + 1] = a2.l;
+        }
+        segs[0][tid] = a1.h; segs[1][tid] = a1.l; segs[2][tid] = a2.h; segs[3][tid] = a2.l;
+        __syncthreads();
+        if (tid < 32) {  // exclusive scan of the 256 segment totals (float-float) by one warp
+          FF c1{0.f, 0.f}, c2{0.f, 0.f};
+          for (int q = 0; q < kScanThreads / 32; ++q) {
+            const int u = q * 32 + tid;
+            FF i1{segs[0][u], segs[1][u]}, i2{segs[2][u], segs[3][u]};
+    #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const FF t1 = ff_shfl_up(i1, o), t2 = ff_shfl_up(i2, o);
+              if (tid >= o) { i1 = ff_add(i1, t1); i2 = ff_add(i2, t2); }
+            }
+            FF e1 = ff_shfl_up(i1, 1), e2 = ff_shfl_up(i2, 1);  // exclusive within the warp
+            if (tid == 0) { e1 = FF{0.f, 0.f}; e2 = FF{0.f, 0.f}; }
+            e1 = ff_add(c1, e1);
+            e2 = ff_add(c2, e2);
+            c1 = ff_add(c1, ff_shfl(i1, 31));
+            c2 = ff_add(c2, ff_shfl(i2, 31));
+            segs[0][u] = e1.h; segs[1][u] = e1.l; segs[2][u] = e2.h; segs[3][u] = e2.l;
+          }
+        }
+        __syncthreads();
+        {
+          const FF o1{segs[0][tid], segs[1][tid]}, o2{segs[2][tid], segs[3][tid]};
+          if (tid == 0) { p1h[0] = 0.f; p1l[0] = 0.f; p2h[0] = 0.f; p2l[0] = 0.f; }
+          for (int p = lo; p < hi; ++p) {
+            const FF v1 = ff_add(o1, FF{p1h[p + 1], p1l[p + 1]});
+            const FF v2 = ff_add(o2, FF{p2h[p + 1], p2l[p + 1]});
+            p1h[p + 1] = v1.h; p1l[p + 1] = v1.l;
+            p2h[p + 1] = v2.h; p2l[p + 1] = v2.l;
+          }
+        }
+        __syncthreads();
+        // ---- window statistics: D = m * sum(y^2) - sum(y)^2 = m^2 var ----
+        // A window whose D is within the prefix sums' rounding of the constant
+        // threshold is decided from its samples: all equal (constant), else the
+        // float64 two-pass variance.
+        const float fm = static_cast<float>(m);
+        const float m_ref = fm * static_cast<float>(x_ref);
+        const float sqrt_m = sqrtf(fm);
+        for (int w = tid; w < nw; w += kScanThreads) {
+          const FF s1 = ff_add(FF{p1h[w + m], p1l[w + m]}, ff_neg(FF{p1h[w], p1l[w]}));
+          const FF s2 = ff_add(FF{p2h[w + m], p2l[w + m]}, ff_neg(FF{p2h[w], p2l[w]}));
+          const FF D = ff_add(ff_mul(s2, fm), ff_neg(ff_sqr(s1)));
+          const float Df = D.h + D.l;
+          const float mmu = m_ref + s1.h;                         // m * window mean
+          const float thr = static_cast<float>(kConstRelVar) * fmaxf(fm * fm, mmu * mmu);
+          const float slack = 0x1p-30f * fm * (p2h[w + m] + p2h[w]);
+          float inv;
+          if (Df > thr + slack) {
+            inv = sqrt_m * rsqrtf(Df);
+          } else {
+            bool equal = true;
+            for (int t = 1; t < m && equal; ++t) equal = (x[w + t] == x[w]);
+            if (equal) {
+              inv = 0.f;
+            } else {
+              double mu = 0.0;
+              for (int t = 0; t < m; ++t) mu += static_cast<double>(x[w + t]);
+              mu /= m;
+              double v = 0.0;
+              for (int t = 0; t < m; ++t) {
+                const double dv = static_cast<double>(x[w + t]) - mu;
+                v += dv * dv;
+              }
+              inv = (v / m <= kConstRelVar * fmax(1.0, mu * mu)) ? 0.f : static_cast<float>(1.0 / sqrt(v));
+            }
+          }
+          w_inv[w] = inv;
+          w_mean[w] = s1.h / fm;
+        }
+        __syncthreads();
+
       }
-      __syncthreads();  // qlist is rewritten by the next batch's selection
+
+      // batches of up to qb discords: staged in groups of four (taps interleaved,
+      // four per 16 bytes), a pair or one; every warp then runs its 256 windows
+      // through each group and merges with one atomic per discord
+      for (int b0 = 0; b0 < total; b0 += qb) {
+        const int nb = min(qb, total - b0);
+        for (int b = 0; b < nb;) {
+          const int nq = (nb - b >= 3) ? 4 : nb - b;
+          float* qs = qbuf + b * m4;
+          auto qsrc = [&](int q) {  // discord b + q's centred query of stream j
+            return a.Q + ((static_cast<int64_t>(s) * a.K + act[b0 + b + q]) * a.d + j) * m4;
+          };
+          if (nq == 4) {
+            const float *q0 = qsrc(0), *q1 = qsrc(1), *q2 = qsrc(2), *q3 = (b + 3 < nb) ? qsrc(3) : nullptr;
+            for (int t = tid; t < m4; t += kScanThreads)
+              *reinterpret_cast<float4*>(qs + 4 * t) = make_float4(q0[t], q1[t], q2[t], q3 ? q3[t] : 0.f);
+          } else if (nq == 2) {
+            const float *q0 = qsrc(0), *q1 = qsrc(1);
+            for (int t = tid; t < m4; t += kScanThreads) *reinterpret_cast<float2*>(qs + 2 * t) = make_float2(q0[t], q1[t]);
+          } else {
+            const float* q0 = qsrc(0);
+            for (int t = tid; t < m4; t += kScanThreads) qs[t] = q0[t];
+          }
+          b += nq;
+        }
+        if (tid < nb) {
+          const int64_t sr = static_cast<int64_t>(s) * a.K + act[b0 + tid];
+          qinf[tid] = a.qinfo[sr * a.d + j];
+          qstar[tid] = a.idx[sr];
+        }
+        __syncthreads();
+        for (int b = 0; b < nb;) {
+          const int nq = (nb - b >= 3) ? 4 : nb - b;
+          float acc[4][kWinPerThread];
+          if (nq == 4)
+            dot_windows<4>(xs, qbuf + b * m4, m4, w0, acc);
+          else if (nq == 2)
+            dot_windows<2>(xs, qbuf + b * m4, m4, w0, acc);
+          else
+            dot_windows<1>(xs, qbuf + b * m4, m4, w0, acc);
+          // this thread's window statistics (read after the products: fewer live registers)
+          float winv[kWinPerThread], wmean[kWinPerThread];
+          {
+            const float4 i0 = *reinterpret_cast<const float4*>(w_inv + w0);
+            const float4 i1 = *reinterpret_cast<const float4*>(w_inv + w0 + 4);
+            const float4 m0 = *reinterpret_cast<const float4*>(w_mean + w0);
+            const float4 m1 = *reinterpret_cast<const float4*>(w_mean + w0 + 4);
+            winv[0] = i0.x; winv[1] = i0.y; winv[2] = i0.z; winv[3] = i0.w;
+            winv[4] = i1.x; winv[5] = i1.y; winv[6] = i1.z; winv[7] = i1.w;
+            wmean[0] = m0.x; wmean[1] = m0.y; wmean[2] = m0.z; wmean[3] = m0.w;
+            wmean[4] = m1.x; wmean[5] = m1.y; wmean[6] = m1.z; wmean[7] = m1.w;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (q < nq && b + q < nb) {
+              const float4 qi = qinf[b + q];
+              const int i_star = qstar[b + q];
+              // this thread's best window for the discord (the first of equal keys), packed once
+              float bk = -FLT_MAX;
+              int bu = -1;
+#pragma unroll
+              for (int u = 0; u < kWinPerThread; ++u) {
+                const int w = w0 + u;
+                const int t = t0 + w;
+                const float inv_t = winv[u];
+                float key;
+                if (qi.w != 0.f) key = (inv_t == 0.f) ? 0.0f : -0.5f;  // rho 1 (dist 0) to a constant window, else 1/2
+                else if (inv_t == 0.f) key = -0.5f;                     // rho 1/2: 2m(1 - 1/2) = m
+                else {
+                  const float cov = __fmaf_rn(-wmean[u], qi.y, acc[q][u]);
+                  key = fminf(0.0f, fmaxf(-2.0f, __fmaf_rn(cov * qi.x, inv_t, -1.0f)));  // rho - 1
+                }
+                const bool ok = w < nw && !(t > i_star - a.excl && t < i_star + a.excl);
+                if (ok && key > bk) {
+                  bk = key;
+                  bu = u;
+                }
+              }
+              unsigned long long best = bu >= 0 ? tsk_pack(bk, t0 + w0 + bu) : 0ull;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(TSK_FULL_MASK, best, o));
+              if (lane == 0 && best)
+                atomicMax(&a.best[(static_cast<int64_t>(s) * a.K + act[b0 + b + q]) * a.d + j], best);
+            }
+          }
+          b += nq;
+        }
+        __syncthreads();  // the staged batch is rewritten by the next one
+      }
     }
     __syncthreads();  // shared buffers are reused by the next item
   }
