@@ -29,7 +29,11 @@
 //                       the best re-scored exactly (compensated sums) where the
 //                       match is close, dist = sqrt(2 m (1 - rho)), plus the
 //                       constant-window rules.
-// After point updates (section 5 below) only the windows covering changed
+//   5. k_mp_rescan      windows with a near-exact match (1 - rho < 1e-4) or an
+//                       overflowed near-tie list: the whole row swept in
+//                       float32, every window within float32 resolution of its
+//                       best re-scored exactly.
+// After point updates (section 6 below) only the windows covering changed
 // samples, and those whose nearest neighbour was among them, are re-profiled.
 // The float64 variant (k_mp_diag_f64) is exact: one thread per diagonal, a
 // first pass takes the float64 maximum per window, a second pass the lowest
@@ -92,8 +96,13 @@ constexpr float kExactRho = 0.99f;
 // A window whose nearest neighbour is within this of rho = 1 (its distance below
 // the bar's floor, where the bar is absolute), or a close match (1 - rho < 5e-3)
 // whose near-tie list overflowed, is re-scanned whole: every window within
-// kRescanTol (in rho) of the best float32 score is re-scored exactly.
+// kRescanTol (in rho) of the best float32 score is re-scored exactly.  Not when
+// the chosen neighbour's exact 1 - rho is at most kRescanExact: its distance,
+// sqrt(2m (1 - rho)) <= 1e-5 sqrt(2m), is already within the bar's absolute
+// floor of any better one (exact repeats, e.g. periodic square waves).
 constexpr double kRescanGap = 1e-4;
+constexpr double kRescanExact = 1e-10;
+constexpr int kRescanThreads = 512;  // one block per listed window: a row's latency is spread over 16 warps
 constexpr float kRescanTol = 4e-6f;
 
 struct WinArrays {
@@ -1082,7 +1091,8 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
       }
       if (j >= 0) dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, best_rho))));
       // near ties decide the bar only for close matches (error ~ 1e-6 / (1 - rho))
-      if (rescan && j >= 0 && (1.0 - best_rho < kRescanGap || (wa.ncnt[wi] > kCand && 1.0 - best_rho < 5e-3)))
+      const double gap = 1.0 - best_rho;
+      if (rescan && j >= 0 && gap > kRescanExact && (gap < kRescanGap || (wa.ncnt[wi] > kCand && gap < 5e-3)))
         rescan[atomicAdd(rescan_n, 1u)] = e;
     }
   }
@@ -1092,26 +1102,29 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
 }
 
 // ---------------------------------------------------------------------------
-// 4'. whole-row rescan of the windows the refinement listed: near-exact matches
+// 5. whole-row rescan of the windows the refinement listed: near-exact matches
 // (distance below the bar's floor) and windows whose near-tie list overflowed.
-// One warp per window: a first float32 sweep over every admissible partner
+// One block per window: a first float32 sweep over every admissible partner
 // window (groups of 8, sliding dot products) finds the best score, a second
 // sweep re-scores exactly (compensated sums) every window within kRescanTol of
 // it.  The exact best, lowest index on ties, replaces the refinement's result;
 // the constant-window rule applies as there.  float32 series only.
 // ---------------------------------------------------------------------------
 template <bool AB>
-__global__ void __launch_bounds__(256) k_mp_rescan(const float* __restrict__ X, const float* __restrict__ X2, int split,
+__global__ void __launch_bounds__(kRescanThreads) k_mp_rescan(const float* __restrict__ X, const float* __restrict__ X2, int split,
                                                    const int64_t* __restrict__ xoff, const int32_t* __restrict__ len,
                                                    const int64_t* __restrict__ woff, int n_streams, int m, int excl,
                                                    WinArrays wa, float* __restrict__ P, int32_t* __restrict__ I,
                                                    float* __restrict__ P2, int32_t* __restrict__ I2,
                                                    const int64_t* __restrict__ rescan,
                                                    const unsigned int* __restrict__ rescan_n) {
-  const int lane = threadIdx.x & 31;
-  const long long nwarps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
+  constexpr int kW = kRescanThreads / 32;
+  __shared__ float skmax[kW];
+  __shared__ double srho[kW];
+  __shared__ int sj[kW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long n = static_cast<long long>(*rescan_n);
-  for (long long r = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nwarps) {
+  for (long long r = blockIdx.x; r < n; r += gridDim.x) {
     const int64_t e = rescan[r];
     const int q = tsk_find_segment<int64_t>(xoff, n_streams, e);
     float* Pout = P;
@@ -1133,9 +1146,9 @@ __global__ void __launch_bounds__(256) k_mp_rescan(const float* __restrict__ X, 
     const double* mup = wa.mu + wbp;
     const float* invp = wa.inv + wbp;
     const int ex = AB ? 0 : excl;
-    // sweep 1: the best float32 score
+    // sweep 1: the best float32 score (the block's threads take groups of 8 windows in turn)
     float kmax = -FLT_MAX;
-    for (int g = lane * kVh; g < lp; g += 32 * kVh) {
+    for (int g = tid * kVh; g < lp; g += kRescanThreads * kVh) {
       float ks[kVh];
       GroupScan<float>::scores(x, i, xp, g, m, mu_i, mup, invp, lp, ex, AB, ks);
 #pragma unroll
@@ -1143,12 +1156,20 @@ __global__ void __launch_bounds__(256) k_mp_rescan(const float* __restrict__ X, 
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) kmax = fmaxf(kmax, __shfl_xor_sync(TSK_FULL_MASK, kmax, o));
-    if (kmax == -FLT_MAX) continue;  // no non-constant partner: the refinement's result stands
+    if (lane == 0) skmax[warp] = kmax;
+    __syncthreads();
+    kmax = skmax[0];
+#pragma unroll
+    for (int w = 1; w < kW; ++w) kmax = fmaxf(kmax, skmax[w]);
+    if (kmax == -FLT_MAX) {  // no non-constant partner: the refinement's result stands
+      __syncthreads();       // skmax is rewritten by the next row
+      continue;
+    }
     const float thr = kmax - kRescanTol / fmaxf(wa.inv[wb + i], FLT_MIN);
     // sweep 2: exact scores of every window within the tolerance
     double brho = -2.0;
     int bj = INT_MAX;
-    for (int g = lane * kVh; g < lp; g += 32 * kVh) {
+    for (int g = tid * kVh; g < lp; g += kRescanThreads * kVh) {
       float ks[kVh];
       GroupScan<float>::scores(x, i, xp, g, m, mu_i, mup, invp, lp, ex, AB, ks);
 #pragma unroll
@@ -1171,30 +1192,43 @@ __global__ void __launch_bounds__(256) k_mp_rescan(const float* __restrict__ X, 
         bj = oj;
       }
     }
-    if (lane == 0 && bj != INT_MAX) {
-      double dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, brho))));
-      int j = bj;
-      // the constant-window rule (lowest admissible constant window at sqrt(m))
-      int jc = -1;
-      if (wa.constcnt[p] > 0) {
-        const int f = wa.nxt[wbp];
-        if (AB) {
-          if (f < lp) jc = f;
-        } else if (f <= i - excl) {
-          jc = f;
-        } else if (i + excl < l) {
-          const int gg = wa.nxt[wb + i + excl];
-          if (gg < l) jc = gg;
-        }
-      }
-      const double sqm = sqrt(static_cast<double>(m));
-      if (jc >= 0 && (sqm < dist || (sqm == dist && jc < j))) {
-        dist = sqm;
-        j = jc;
-      }
-      Pout[eo] = static_cast<float>(dist);
-      Iout[eo] = j;
+    if (lane == 0) {
+      srho[warp] = brho;
+      sj[warp] = bj;
     }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < kW; ++w)
+        if (srho[w] > brho || (srho[w] == brho && sj[w] < bj)) {
+          brho = srho[w];
+          bj = sj[w];
+        }
+      if (bj != INT_MAX) {
+        double dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, brho))));
+        int j = bj;
+        // the constant-window rule (lowest admissible constant window at sqrt(m))
+        int jc = -1;
+        if (wa.constcnt[p] > 0) {
+          const int f = wa.nxt[wbp];
+          if (AB) {
+            if (f < lp) jc = f;
+          } else if (f <= i - excl) {
+            jc = f;
+          } else if (i + excl < l) {
+            const int gg = wa.nxt[wb + i + excl];
+            if (gg < l) jc = gg;
+          }
+        }
+        const double sqm = sqrt(static_cast<double>(m));
+        if (jc >= 0 && (sqm < dist || (sqm == dist && jc < j))) {
+          dist = sqm;
+          j = jc;
+        }
+        Pout[eo] = static_cast<float>(dist);
+        Iout[eo] = j;
+      }
+    }
+    __syncthreads();  // skmax, srho and sj are rewritten by the next row
   }
 }
 
@@ -1338,13 +1372,13 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
     TSK_LAUNCH_CHECK(ctx, "k_mp_refine");
     if constexpr (std::is_same<TX, float>::value) {
       if (rescan) {
-        const unsigned gr = static_cast<unsigned>(ctx->sm_count * 8);
+        const unsigned gr = static_cast<unsigned>(ctx->sm_count * 2);  // two resident blocks per SM
         if (ab)
-          k_mp_rescan<true><<<gr, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.woff, n_streams, m, excl, wa,
+          k_mp_rescan<true><<<gr, kRescanThreads, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.woff, n_streams, m, excl, wa,
                                                 static_cast<float*>(P), I, static_cast<float*>(P2), I2, rescan,
                                                 rescan_n);
         else
-          k_mp_rescan<false><<<gr, 256, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.woff, n_streams, m, excl,
+          k_mp_rescan<false><<<gr, kRescanThreads, 0, st>>>(X, X2, split, plan.xoff, plan.len, plan.woff, n_streams, m, excl,
                                                  wa, static_cast<float*>(P), I, nullptr, nullptr, rescan, rescan_n);
         TSK_LAUNCH_CHECK(ctx, "k_mp_rescan");
       }
@@ -1354,7 +1388,7 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
 }
 
 // ---------------------------------------------------------------------------
-// 5. incremental profile after point updates (Sec. III-C point updates; the
+// 6. incremental profile after point updates (Sec. III-C point updates; the
 //    streaming use of Sec. III-B)
 //
 // A sample t that changes moves the windows t-m+1 .. t (the affected set A).
@@ -1698,7 +1732,7 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
                                                        n_streams, total, m, excl, 0, wa, P, I, nullptr, nullptr, 1,
                                                        rescan, rescan_n);
   TSK_LAUNCH_CHECK(ctx, "k_mp_refine");
-  k_mp_rescan<false><<<static_cast<unsigned>(ctx->sm_count * 8), 256, 0, st>>>(
+  k_mp_rescan<false><<<static_cast<unsigned>(ctx->sm_count * 2), kRescanThreads, 0, st>>>(
       X, X, n_streams, plan.xoff, plan.len, plan.woff, n_streams, m, excl, wa, P, I, nullptr, nullptr, rescan, rescan_n);
   TSK_LAUNCH_CHECK(ctx, "k_mp_rescan");
   return TSK_OK;
@@ -1959,7 +1993,7 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
       X, X, 1, dh->xoff, dh->len, dh->smask, dh->woff, 1, n, m, excl, 0, wa, P, I, nullptr, nullptr, 0, rescan,
       rescan_n);
   if (!launched()) return TSK_ERR_CUDA;
-  k_mp_rescan<false><<<static_cast<unsigned>(sms * 8), 256, 0, stream>>>(X, X, 1, dh->xoff, dh->len, dh->woff, 1, m,
+  k_mp_rescan<false><<<static_cast<unsigned>(sms * 2), kRescanThreads, 0, stream>>>(X, X, 1, dh->xoff, dh->len, dh->woff, 1, m,
                                                                          excl, wa, P, I, nullptr, nullptr, rescan,
                                                                          rescan_n);
   if (!launched()) return TSK_ERR_CUDA;
