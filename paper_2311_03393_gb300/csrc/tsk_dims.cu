@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
   float* p1l = p1h + (kTW + m);
   float* p2h = p1l + (kTW + m);                                // [kTW + m] prefix of their squares
   float* p2l = p2h + (kTW + m);
-  __shared__ float segs[4][kScanThreads];
+  __shared__ float segs[4][kScanThreads / 32];  // per-warp totals of the prefix scan
   __shared__ int act[kScanThreads];  // active discords r of the item (ascending), up to 256 at a time
   __shared__ int wcnt[kScanThreads / 32];
   __shared__ float4 qinf[kQB];
@@ -335,37 +335,28 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_dd_scan(const TX* __restric
           p1h[p + 1] = a1.h; p1l[p + 1] = a1.l;
           p2h[p + 1] = a2.h; p2l[p + 1] = a2.l;
         }
-        segs[0][tid] = a1.h; segs[1][tid] = a1.l; segs[2][tid] = a2.h; segs[3][tid] = a2.l;
-        __syncthreads();
-        if (tid < 32) {  // exclusive scan of the 256 segment totals (float-float) by one warp
-          FF c1{0.f, 0.f}, c2{0.f, 0.f};
-          for (int q = 0; q < kScanThreads / 32; ++q) {
-            const int u = q * 32 + tid;
-            FF i1{segs[0][u], segs[1][u]}, i2{segs[2][u], segs[3][u]};
-    #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const FF t1 = ff_shfl_up(i1, o), t2 = ff_shfl_up(i2, o);
-              if (tid >= o) { i1 = ff_add(i1, t1); i2 = ff_add(i2, t2); }
-            }
-            FF e1 = ff_shfl_up(i1, 1), e2 = ff_shfl_up(i2, 1);  // exclusive within the warp
-            if (tid == 0) { e1 = FF{0.f, 0.f}; e2 = FF{0.f, 0.f}; }
-            e1 = ff_add(c1, e1);
-            e2 = ff_add(c2, e2);
-            c1 = ff_add(c1, ff_shfl(i1, 31));
-            c2 = ff_add(c2, ff_shfl(i2, 31));
-            segs[0][u] = e1.h; segs[1][u] = e1.l; segs[2][u] = e2.h; segs[3][u] = e2.l;
-          }
+        // exclusive scan of the 256 segment totals (float-float): each warp scans its
+        // 32 in registers, then adds the totals of the warps before it
+        FF i1 = a1, i2 = a2;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const FF t1 = ff_shfl_up(i1, o), t2 = ff_shfl_up(i2, o);
+          if (lane >= o) { i1 = ff_add(i1, t1); i2 = ff_add(i2, t2); }
         }
+        if (lane == 31) { segs[0][warp] = i1.h; segs[1][warp] = i1.l; segs[2][warp] = i2.h; segs[3][warp] = i2.l; }
+        FF o1 = ff_shfl_up(i1, 1), o2 = ff_shfl_up(i2, 1);  // exclusive within the warp
+        if (lane == 0) { o1 = FF{0.f, 0.f}; o2 = FF{0.f, 0.f}; }
         __syncthreads();
-        {
-          const FF o1{segs[0][tid], segs[1][tid]}, o2{segs[2][tid], segs[3][tid]};
-          if (tid == 0) { p1h[0] = 0.f; p1l[0] = 0.f; p2h[0] = 0.f; p2l[0] = 0.f; }
-          for (int p = lo; p < hi; ++p) {
-            const FF v1 = ff_add(o1, FF{p1h[p + 1], p1l[p + 1]});
-            const FF v2 = ff_add(o2, FF{p2h[p + 1], p2l[p + 1]});
-            p1h[p + 1] = v1.h; p1l[p + 1] = v1.l;
-            p2h[p + 1] = v2.h; p2l[p + 1] = v2.l;
-          }
+        for (int v = 0; v < warp; ++v) {
+          o1 = ff_add(o1, FF{segs[0][v], segs[1][v]});
+          o2 = ff_add(o2, FF{segs[2][v], segs[3][v]});
+        }
+        if (tid == 0) { p1h[0] = 0.f; p1l[0] = 0.f; p2h[0] = 0.f; p2l[0] = 0.f; }
+        for (int p = lo; p < hi; ++p) {
+          const FF v1 = ff_add(o1, FF{p1h[p + 1], p1l[p + 1]});
+          const FF v2 = ff_add(o2, FF{p2h[p + 1], p2l[p + 1]});
+          p1h[p + 1] = v1.h; p1l[p + 1] = v1.l;
+          p2h[p + 1] = v2.h; p2l[p + 1] = v2.l;
         }
         __syncthreads();
         // ---- window statistics: D = m * sum(y^2) - sum(y)^2 = m^2 var ----
