@@ -1203,6 +1203,16 @@ __global__ void __launch_bounds__(kRescanThreads) k_mp_rescan(const float* __res
           brho = srho[w];
           bj = sj[w];
         }
+      {  // the refinement's own neighbour stays a candidate (never a worse result)
+        const int j0 = Iout[eo];
+        if (j0 >= 0 && j0 < lp && (AB || abs(i - j0) >= excl) && invp[j0] != 0.f) {
+          const double rho0 = tsk::window_rho(x, i, xp, j0, m, mu_i, mup[j0]);
+          if (rho0 > brho || (rho0 == brho && j0 < bj)) {
+            brho = rho0;
+            bj = j0;
+          }
+        }
+      }
       if (bj != INT_MAX) {
         double dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, brho))));
         int j = bj;
