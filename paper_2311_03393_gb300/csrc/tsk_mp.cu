@@ -93,15 +93,27 @@ constexpr float kCloseKey = 0.02f;
 // correlation reaches this; below it float32 (~1e-6 in rho) gives the distance
 // to ~1e-4 relative (dist error ~ drho / (2 (1 - rho))), a tenth of the 1e-3 bar.
 constexpr float kExactRho = 0.99f;
-// A window whose nearest neighbour is within this of rho = 1 (its distance below
-// the bar's floor, where the bar is absolute), or a close match (1 - rho < 5e-3)
-// whose near-tie list overflowed, is re-scanned whole: every window within
-// kRescanTol (in rho) of the best float32 score is re-scored exactly.  Not when
-// the chosen neighbour's exact 1 - rho is at most kRescanExact: its distance,
-// sqrt(2m (1 - rho)) <= 1e-5 sqrt(2m), is already within the bar's absolute
-// floor of any better one (exact repeats, e.g. periodic square waves).
-constexpr double kRescanGap = 1e-4;
+// A window whose nearest neighbour is within this of rho = 1, or a close match
+// (1 - rho < 5e-3) whose near-tie list overflowed, is re-scanned whole: every
+// window within kRescanTol (in rho) of the best float32 score is re-scored
+// exactly.  Choosing a neighbour d_rho worse moves the distance by about
+// d_rho / (2 (1 - rho)) of itself, so near ties that float32 orders only to
+// ~1e-6 (up to ~2e-6 over the longest walks) can break the 1e-3 bar wherever
+// 1 - rho < 1e-3; those rows do not rely on the near-tie lists, whose content
+// depends on the order of the merges.  Not when the chosen neighbour's exact
+// 1 - rho is at most kRescanExact: its distance, sqrt(2m (1 - rho)) <=
+// 1e-5 sqrt(2m), is already within the bar's absolute floor of any better one
+// (exact repeats, e.g. periodic square waves).
+constexpr double kRescanGap = 1e-3;
 constexpr double kRescanExact = 1e-10;
+// A window whose norm ||x - mean|| is below this fraction of the largest in
+// its stream or its partner's is re-scanned too.  The float32 recurrence keeps
+// an absolute error set by the loud windows of a walk (~2^-24 of their
+// covariances); relative to a window a thousand times quieter (a flat stretch
+// with sensor noise between steps or spikes) that error reorders its
+// candidates.  The re-scan's float32 scores come from centred values, not the
+// recurrence, so they resolve such windows.
+constexpr float kQuietNorm = 1e-2f;
 constexpr int kRescanThreads = 512;  // one block per listed window: a row's latency is spread over 16 warps
 constexpr float kRescanTol = 4e-6f;
 
@@ -114,6 +126,7 @@ struct WinArrays {
   unsigned long long* best;   // packed (key, first window of the best candidate group)
   int32_t* nxt;
   int32_t* constcnt;
+  unsigned int* nmax;         // per stream: the largest window norm ||x - mean|| (float bits)
   int32_t* ncnt;              // near-tie groups offered per window (may exceed kCand)
   unsigned long long* near;   // [window][kCand] near-tie groups, packed like best
   double* inv64;   // float64 mode only
@@ -159,6 +172,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restri
   extern __shared__ double sm[];
   __shared__ double scan_sh[64];
   __shared__ int ccount;
+  __shared__ unsigned int bnmax;
   const int q = tsk_find_segment<int64_t>(chunk_prefix, n_streams, static_cast<int64_t>(blockIdx.x));
   const int n = len[q];
   const int l = n - m + 1;
@@ -169,7 +183,10 @@ __global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restri
   const int64_t wb = woff[q];
   double* E1 = sm;             // E1[u] = sum of the first u shifted samples
   double* E2 = sm + (ns + 1);
-  if (threadIdx.x == 0) ccount = 0;
+  if (threadIdx.x == 0) {
+    ccount = 0;
+    bnmax = 0u;
+  }
   const double xref = static_cast<double>(x[w0]);
   bool bad = false;
   for (int u = threadIdx.x; u < ns; u += kWinThreads) {
@@ -198,6 +215,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restri
   __syncthreads();
   const double inv_m = 1.0 / m;
   int my_const = 0;
+  float my_nmax = 0.f;
   for (int u = threadIdx.x; u < nw; u += kWinThreads) {
     const int i = w0 + u;
     const double t1 = E1[u + m] - E1[u];
@@ -208,6 +226,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restri
     const bool cst = ss * inv_m <= kConstRelVar * fmax(1.0, mu * mu);
     my_const += cst ? 1 : 0;
     const double r = cst ? 0.0 : rsqrt(ss);
+    if (!cst) my_nmax = fmaxf(my_nmax, static_cast<float>(sqrt(ss)));
     float df = 0.f, dg = 0.f;
     if (i < l - 1) {
       const double xa = static_cast<double>(x[i]), xb = static_cast<double>(x[i + m]);
@@ -235,10 +254,19 @@ __global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restri
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_const += __shfl_xor_sync(TSK_FULL_MASK, my_const, o);
-  if ((threadIdx.x & 31) == 0 && my_const) atomicAdd(&ccount, my_const);
+  for (int o = 16; o > 0; o >>= 1) {
+    my_const += __shfl_xor_sync(TSK_FULL_MASK, my_const, o);
+    my_nmax = fmaxf(my_nmax, __shfl_xor_sync(TSK_FULL_MASK, my_nmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (my_const) atomicAdd(&ccount, my_const);
+    atomicMax(&bnmax, __float_as_uint(my_nmax));  // non-negative floats order as their bits
+  }
   __syncthreads();
-  if (threadIdx.x == 0 && ccount) atomicAdd(&wa.constcnt[q], ccount);
+  if (threadIdx.x == 0) {
+    if (ccount) atomicAdd(&wa.constcnt[q], ccount);
+    atomicMax(&wa.nmax[q], bnmax);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1063,9 +1091,9 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
       int nv = 0;
       float rmax = -2.f;
       const float inv_i = wa.inv[wb + i];
-      for (int e = 0; e < ng; ++e) {
+      for (int c = 0; c < ng; ++c) {
         float kg = 0.f;
-        const int jg = GroupScan<TX>::best(x, i, xp, grp[e], m, wa.mu[wb + i], mup, invp, lp, excl, AB, &kg);
+        const int jg = GroupScan<TX>::best(x, i, xp, grp[c], m, wa.mu[wb + i], mup, invp, lp, excl, AB, &kg);
         if (jg < 0) continue;
         gj[nv] = jg;
         gr[nv] = kg * inv_i;
@@ -1075,24 +1103,28 @@ __global__ void __launch_bounds__(256) k_mp_refine(const TX* __restrict__ X, con
       double best_rho = -2.0;
       if (rmax < kExactRho) {
         // no close match: float32 resolves rho to ~1e-6, 1e-5 of the distance
-        for (int e = 0; e < nv; ++e)
-          if (gr[e] > best_rho || (gr[e] == best_rho && gj[e] < j)) {
-            best_rho = gr[e];
-            j = gj[e];
+        for (int c = 0; c < nv; ++c)
+          if (gr[c] > best_rho || (gr[c] == best_rho && gj[c] < j)) {
+            best_rho = gr[c];
+            j = gj[c];
           }
       } else {
-        for (int e = 0; e < nv; ++e) {
-          const double rho = tsk::window_rho(x, i, xp, gj[e], m, wa.mu[wb + i], mup[gj[e]]);
-          if (rho > best_rho || (rho == best_rho && gj[e] < j)) {
+        for (int c = 0; c < nv; ++c) {
+          const double rho = tsk::window_rho(x, i, xp, gj[c], m, wa.mu[wb + i], mup[gj[c]]);
+          if (rho > best_rho || (rho == best_rho && gj[c] < j)) {
             best_rho = rho;
-            j = gj[e];
+            j = gj[c];
           }
         }
       }
       if (j >= 0) dist = sqrt(fmax(0.0, 2.0 * m * (1.0 - fmin(1.0, best_rho))));
-      // near ties decide the bar only for close matches (error ~ 1e-6 / (1 - rho))
+      // near ties decide the bar only for close matches (error ~ 1e-6 / (1 - rho));
+      // a quiet window's keys carry the recurrence's error of the loud ones
       const double gap = 1.0 - best_rho;
-      if (rescan && j >= 0 && gap > kRescanExact && (gap < kRescanGap || (wa.ncnt[wi] > kCand && gap < 5e-3)))
+      const float nloud = fmaxf(__uint_as_float(wa.nmax[q]), __uint_as_float(wa.nmax[p]));
+      const bool quiet = wa.inv[wi] > 0.f && kQuietNorm * nloud * wa.inv[wi] > 1.f;
+      if (rescan && j >= 0 && gap > kRescanExact &&
+          (gap < kRescanGap || (wa.ncnt[wi] > kCand && gap < 5e-3) || quiet))
         rescan[atomicAdd(rescan_n, 1u)] = e;
     }
   }
@@ -1284,6 +1316,7 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
   wa.best = cv.take<unsigned long long>(W);
   wa.nxt = cv.take<int32_t>(W);
   wa.constcnt = cv.take<int32_t>(n_streams);
+  wa.nmax = cv.take<unsigned int>(n_streams);
   if (!f64) {
     wa.ncnt = cv.take<int32_t>(W);
     wa.near = cv.take<unsigned long long>(W * kCand);
@@ -1304,6 +1337,7 @@ tsk_status run_typed(tsk_ctx* ctx, const TX* X, const TX* X2, int32_t split, boo
   if (rescan_n) TSK_CUDA_TRY(ctx, cudaMemsetAsync(rescan_n, 0, sizeof(unsigned int), st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.best, 0, sizeof(unsigned long long) * W, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.constcnt, 0, sizeof(int32_t) * n_streams, st));
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.nmax, 0, sizeof(unsigned int) * n_streams, st));
   if (!f64) TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.ncnt, 0, sizeof(int32_t) * W, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   if (f64) TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.bidx, 0x7f, sizeof(int32_t) * W, st));  // ~INT_MAX
@@ -1661,6 +1695,7 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
   wa.best = cv.take<unsigned long long>(W);
   wa.nxt = cv.take<int32_t>(W);
   wa.constcnt = cv.take<int32_t>(n_streams);
+  wa.nmax = cv.take<unsigned int>(n_streams);
   wa.ncnt = cv.take<int32_t>(W);
   wa.near = cv.take<unsigned long long>(W * kCand);
   unsigned long long* counter = cv.take<unsigned long long>(1);  // diagonal-kernel claims
@@ -1674,6 +1709,7 @@ tsk_status run_update(tsk_ctx* ctx, const float* X, int32_t n_streams, const int
   cudaStream_t st = ctx->stream;
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(aflag, 0, static_cast<size_t>(W), st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.constcnt, 0, sizeof(int32_t) * n_streams, st));
+  TSK_CUDA_TRY(ctx, cudaMemsetAsync(wa.nmax, 0, sizeof(unsigned int) * n_streams, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(rcount, 0, sizeof(int32_t) * n_streams, st));
   TSK_CUDA_TRY(ctx, cudaMemsetAsync(rescan_n, 0, sizeof(unsigned int), st));
@@ -1755,7 +1791,7 @@ size_t update_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams, size_t n_runs
          tsk_carver::bytes_for(W * kCand, 8) + tsk_carver::bytes_for(1, 8) + tsk_carver::bytes_for(n_streams, 4) +
          tsk_carver::bytes_for(W, 1) + tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(W, 8) +
          tsk_carver::bytes_for(1, 4) + tsk_carver::bytes_for(n_runs, 16) + tsk_carver::bytes_for(n_tiles_max, 16) +
-         4096;
+         tsk_carver::bytes_for(n_streams, 4) + 4096;
 }
 
 }  // namespace
@@ -1769,7 +1805,7 @@ size_t tsk_mp_ws_bytes(const tsk_mp_plan& plan, int32_t n_streams) {
   const size_t W = static_cast<size_t>(plan.total_windows);
   size_t b = 0;
   b += tsk_carver::bytes_for(W, 8) * 2 + tsk_carver::bytes_for(W, 4) * 3 + tsk_carver::bytes_for(W, 8) +
-       tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_streams, 4) + tsk_carver::bytes_for(1, 8);
+       tsk_carver::bytes_for(W, 4) + tsk_carver::bytes_for(n_streams, 4) * 2 + tsk_carver::bytes_for(1, 8);
   if (plan.prec == TSK_MP_FP64)
     b += tsk_carver::bytes_for(W, 8) + tsk_carver::bytes_for(W, 4);
   else
@@ -1927,7 +1963,7 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   const size_t o_ncnt = off; off = align256(off + 4 * W);
   const size_t o_near = off; off = align256(off + 8 * kCand * W);
   const size_t o_rescan = off; off = align256(off + 8 * W);
-  const size_t o_small = off; off = align256(off + 64);  // constcnt, counter, error word, rescan count
+  const size_t o_small = off; off = align256(off + 64);  // constcnt, counter, error word, rescan count, nmax
   const size_t o_tiles = off; off = align256(off + sizeof(int4) * n_tiles);
   if (off > kStaticScratchBytes) return TSK_ERR_INVALID_ARG;
   char* sb = static_cast<char*>(base);
@@ -1960,6 +1996,7 @@ extern "C" TSK_API tsk_status mp_selfjoin_static(const float* X, int32_t n, int3
   wa.ncnt = reinterpret_cast<int32_t*>(sb + o_ncnt);
   wa.near = reinterpret_cast<unsigned long long*>(sb + o_near);
   wa.constcnt = reinterpret_cast<int32_t*>(sb + o_small);
+  wa.nmax = reinterpret_cast<unsigned int*>(sb + o_small + 28);
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(sb + o_small + 8);
   int* err = reinterpret_cast<int*>(sb + o_small + 16);
 
