@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_stats(const TX* __restri
     const bool cst = ss * inv_m <= kConstRelVar * fmax(1.0, mu * mu);
     my_const += cst ? 1 : 0;
     const double r = cst ? 0.0 : rsqrt(ss);
-    if (!cst) my_nmax = fmaxf(my_nmax, static_cast<float>(sqrt(ss)));
+    if (!cst) my_nmax = fmaxf(my_nmax, static_cast<float>(ss * r));  // ||x - mean|| = ss / sqrt(ss)
     float df = 0.f, dg = 0.f;
     if (i < l - 1) {
       const double xa = static_cast<double>(x[i]), xb = static_cast<double>(x[i + m]);

@@ -467,3 +467,35 @@ def test_near_exact_repeats_meet_the_tolerance(tsk):
     for x, (P, I) in zip(xs, out):
         l = len(x) - m + 1
         check_profile(x.astype(np.float64), m, excl, P[:l], I[:l], rows=np.arange(0, l, 3))
+
+
+def test_quiet_windows_between_steps_and_spikes(tsk):
+    """Flat stretches with sensor noise next to steps (noise 1e-3 of the step) and between sparse
+    spikes (noise 1e-4): windows a thousand times quieter than the stream's loudest, whose keys the
+    float32 recurrence cannot order; they are re-scanned from centred values."""
+    rng = np.random.default_rng(71)
+    n = 6000
+    steps = np.repeat(rng.integers(0, 5, n // 50 + 1), 50)[:n].astype(float) + 1e-3 * rng.normal(size=n)
+    spikes = np.zeros(n)
+    spikes[rng.integers(0, n, 60)] = 1.0
+    spikes += 1e-4 * rng.normal(size=n)
+    for x, m in ((steps, 64), (spikes, 32)):
+        x = x.astype(np.float32)
+        excl = int(math.ceil(m / 4))
+        (P, I), = _streams(tsk, [x], m, excl)
+        l = len(x) - m + 1
+        check_profile(x.astype(np.float64), m, excl, P[:l], I[:l], rows=np.arange(0, l, 3))
+
+
+def test_near_ties_just_above_the_floor_are_stable(tsk):
+    """A sine with noise 1e-2 (1 - rho ~ 1e-4 with ~100 near-repeats per window, within float32's
+    resolution of each other): the same input profiled four times meets the bar every time."""
+    rng = np.random.default_rng(72)
+    n, m = 6000, 40
+    x = (np.sin(2 * np.pi * np.arange(n) / 50) + 1e-2 * rng.normal(size=n)).astype(np.float32)
+    excl = int(math.ceil(m / 4))
+    l = n - m + 1
+    rows = np.arange(0, l, 4)
+    for _ in range(4):
+        (P, I), = _streams(tsk, [x], m, excl)
+        check_profile(x.astype(np.float64), m, excl, P[:l], I[:l], rows=rows)
